@@ -1,0 +1,48 @@
+"""The pins are sensitive: plant plausible mistakes in a copy of the oracle and check that the pin
+suite fails for every one of them (CPU only; the mutated copy is built in a temporary folder)."""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTATIONS = {
+    "eq11_sign": ("(image[pa * C + c] - image[pb * C + c])", "(image[pb * C + c] - image[pa * C + c])"),
+    "eq11_half": ("dLdp += 0.5 * (", "dLdp += 1.0 * ("),
+    "overhang_foreground": ("fg = a_in_b ? 0 : 1;", "fg = a_in_b ? 1 : 0;"),
+    "eq12_sign": ("double dpdr_a = -nB[1] / den_a;", "double dpdr_a = nB[1] / den_a;"),
+    "eq12_slice_axis": ("double nA[2] = {NA[axis], NA[2]}", "double nA[2] = {NA[1 - axis], NA[2]}"),
+    "gather_pixel": ("else gather(scr, tris, tb, xb, yb, g, grad_scr);", "else gather(scr, tris, tb, xa, ya, g, grad_scr);"),
+    "perspective_bary": ("b[i] = ddiv(dmul(lam[i], z[i]), s);", "b[i] = lam[i];"),
+    "depth_derivative": ("I[sh->depth_ch] = ddiv(dconst(1.0), s);", "I[sh->depth_ch] = dconst(1.0 / s.v);"),
+    "dual_quotient_rule": ("(a.d[k] * b.v - a.v * b.d[k])", "(a.d[k] * b.v + a.v * b.d[k])"),
+    "texture_fraction": ("dual fx = dsub(x, dconst(x0));", "dual fx = dconst(x.v - x0);"),
+    "top_left_rule": ("if (!(ga > 0 || (ga == 0 && gb > 0))) return 0;", "if (!(ga >= 0)) return 0;"),
+    "depth_tie_break": ("(z == z1[p] && t < index[p])", "(z == z1[p] && t > index[p])"),
+    "projection_operand": ("xs = (cam->fx * Xc) * zeta + cam->cx;", "xs = (cam->fx * Yc) * zeta + cam->cx;"),
+    "project_backward_transpose": ("grad_verts[3 * v + 0] += R[0] * gX + R[3] * gY + R[6] * gZ;",
+                                   "grad_verts[3 * v + 0] += R[0] * gX + R[1] * gY + R[2] * gZ;"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    mutated = tmp_path / "oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "liboracle_mut.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(lib),
+                    str(mutated), "-lm"], check=True)
+    env = dict(os.environ, ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"
