@@ -1,0 +1,188 @@
+/*
+ * mer.h -- C-ABI of the GB300 micro-edge rasterizer-gradient library (libmer.so).
+ *
+ * Method: "Rasterized Edge Gradients: Handling Discontinuities Differentiably"
+ * (EdgeGrad, arXiv 2405.02508).  Forward: an unmodified z-buffered triangle
+ * rasterizer (index, depth, barycentrics) and deferred shading (interpolated
+ * attributes, bilinear texture, coverage mask, depth).  Backward: the micro-edge
+ * term -- for every horizontally or vertically adjacent pixel pair whose
+ * triangle ids differ, dL/dp = 1/2 (dL/dI_A + dL/dI_B)(I_A - I_B) (Eq. 11),
+ * scattered to the fragments through dp/dr (Sec. 4.3 overhang rule, Eq. 12 for
+ * intersections) and gathered to the vertices (Sec. 4.2) -- on top of the
+ * interior (smooth) term Omega (Eq. 5).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every pointer argument except where stated is a DEVICE pointer.  The caller
+ *   owns all memory, including the workspace; the library allocates nothing.
+ * - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *   NULL = the legacy default stream).  A call returns MER_OK after queueing its
+ *   kernels; argument errors found on the host return at once, without launching.
+ *   Errors found on the device (bin overflow, triangle index >= V, index image
+ *   entry >= T) set bits of the workspace status word, read by mer_sync_status.
+ * - Images are row-major [n, H, W] or [n, H, W, C] (NHWC), float32 unless
+ *   stated.  Pixel (x, y) has its centre at (x + 1/2, y + 1/2); y points down.
+ *   index = -1 marks background.
+ * - Gradient outputs ACCUMULATE (+=); zero them first.
+ * - Sizes: 1 <= H, W <= 8192; V, T < 2^31; n * H * W < 2^31.
+ */
+#ifndef MER_H
+#define MER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+enum {
+    MER_OK = 0,
+    MER_EINVAL = 1,    /* bad argument (null pointer, size out of range, bad option) */
+    MER_ECUDA = 2,     /* a CUDA launch or runtime call failed */
+    MER_EOVERFLOW = 3, /* the bin list did not fit in the workspace (mer_sync_status) */
+    MER_ERANGE = 4     /* a triangle or index-image entry was out of range (mer_sync_status) */
+};
+
+/* Pinhole camera, OpenCV convention (+X right, +Y down, +Z forward), 136 bytes.
+ * X_c = R X_w + t; x_s = fx X_c / Z_c + cx; y_s = fy Y_c / Z_c + cy; zeta = 1 / Z_c.
+ * Triangles with a vertex at Z_c <= znear are not drawn (vertex transform
+ * module, Supp. B). */
+typedef struct mer_camera {
+    double R[9]; /* row-major */
+    double t[3];
+    double fx, fy, cx, cy;
+    double znear;
+} mer_camera;
+
+/* Projected vertex record, 32 bytes, one per (view, vertex).  The screen position
+ * is x_s = X/256 + rx, y_s = Y/256 + ry: X, Y are the positions snapped to 1/256
+ * px (round half to even) that decide coverage; rx, ry are the sub-snap
+ * residuals that keep values and derivatives on the unsnapped geometry.
+ * zeta = 1/Z_c is split as zeta + zeta_lo (float + float residual).
+ * flags: bit 0 = in front of the near plane, bit 1 = inside the guard band
+ * |X|, |Y| <= 2^29; a triangle is drawn only if all its vertices have both. */
+typedef struct mer_vertex {
+    int32_t X, Y;
+    float rx, ry;
+    float zeta, zeta_lo;
+    uint32_t flags;
+    float pad;
+} mer_vertex;
+
+/* Layout of the shaded image [n,H,W,C] (deferred shading, Supp. B).
+ * Channels [0, n_main) hold interpolated attribute channels 0..n_main-1
+ * (uv_offset < 0), or the bilinear texture [tex_h, tex_w, n_main] sampled at the
+ * interpolated (u, v) = attribute channels (uv_offset, uv_offset+1) with u
+ * wrapping and v clamped, texel centres at ((i+1/2)/tex_w, (j+1/2)/tex_h).
+ * mask_ch / depth_ch (or -1) hold the coverage mask (1 on triangles) and the
+ * depth Z.  Attributes are interpolated perspective-correctly. */
+typedef struct mer_shading {
+    int n_main;
+    int C;
+    int uv_offset;
+    int mask_ch;
+    int depth_ch;
+    int C_attr;  /* channels per vertex of `attr` */
+    int tex_h, tex_w;
+} mer_shading;
+
+/* Terms computed by mer_backward (bit mask). */
+enum {
+    MER_EDGE = 1,      /* micro-edge term (Eq. 11, Sec. 4.3, Eq. 12) */
+    MER_INTERIOR = 2,  /* interior term Omega through barycentrics/interpolation/texture */
+    MER_INTERSECT = 4  /* scatter at geometry intersections (Eq. 12); off = the paper's ablation */
+};
+
+const char* mer_strerror(int code);
+int mer_version(void);
+
+/* Bytes of workspace mer_rasterize needs for these sizes.  Zero the first 256
+ * bytes (the status header) once before the first use.  `tile` is the bin
+ * tile edge in pixels (8, 16 or 32); `bin_capacity` is the number of
+ * (triangle, tile) entries to reserve, 0 for the default 4*n*T + 2*n*tiles.
+ * The workspace must be 256-byte aligned. */
+size_t mer_workspace_size(int V, int T, int n, int H, int W, int tile, int64_t bin_capacity);
+
+/* Vertex transform (Supp. B): world vertices [V,3] and cameras [n] (device) ->
+ * projected vertex records vpix [n,V].  FP64 with a fixed operation order and
+ * correctly rounded operations, so the snapped positions are reproducible. */
+int mer_project(const float* verts, int V, const mer_camera* cams, int n, mer_vertex* vpix, void* stream);
+
+/* Screen-space input path: scr [n,V,3] float64 (x_s, y_s, zeta) -> vpix [n,V].
+ * A vertex with zeta <= 0 is behind the camera. */
+int mer_project_screen(const double* scr, int V, int n, mer_vertex* vpix, void* stream);
+
+/* Rasterization module with z-buffer (Supp. B): tile binning and raster.
+ * tris [T,3] int32.  Outputs index [n,H,W] int32 (-1 = background), and
+ * optionally depth [n,H,W] (Z, 0 on background) and bary [n,H,W,2]
+ * (perspective-correct b1, b2); pass NULL to skip them (the other calls never
+ * read bary: they re-derive barycentrics from index + vpix).
+ * Fill rule: a pixel centre is covered iff s*E_i > 0 for all three edge
+ * functions E_i = cross(v_j - P, v_k - P) of the snapped positions (s = sign of
+ * the area; both windings drawn), or E_i == 0 on a top-left edge.  Depth test:
+ * largest zeta_test = sum_i E_i zeta_i / sum_i E_i, ties to the lower id.
+ * The workspace keeps the bins; its contents are not needed afterwards. */
+int mer_rasterize(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
+                  int tile, void* workspace, size_t workspace_bytes,
+                  int32_t* index, float* depth, float* bary, void* stream);
+
+/* Interpolation module + deferred shading (Supp. B): shaded image [n,H,W,C]
+ * per `shading`; background pixels take bg[c] (host array of C floats, copied
+ * into the kernel arguments).  attr [V, C_attr]; tex [tex_h, tex_w, n_main] or
+ * NULL when uv_offset < 0. */
+int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
+              const int32_t* index, const float* attr, const float* tex, const float* bg_host,
+              const mer_shading* shading_host, float* image, void* status_ws, void* stream);
+
+/* Backward pass.  image / grad_image [n,H,W,C] are the shaded image passed
+ * through the edge-gradient step and dL/d(image).  terms = MER_EDGE |
+ * MER_INTERIOR | MER_INTERSECT (any subset).
+ *   MER_EDGE: every pair (x,y)-(x+1,y), (x,y)-(x,y+1) with differing ids:
+ *     Eq. 11 summed over channels; classification by the exact coverage test of
+ *     each pixel centre against the other pixel's triangle (Sec. 4.3): none ->
+ *     adjacent (no scatter), one -> overhang (the triangle on top, whose own
+ *     pixel centre lies inside the other triangle, gets dp/dr = 1 on the pair
+ *     axis), both -> intersection (Eq. 12 in the (axis, zeta) slice for each
+ *     side with the other fixed).  Fragment gradients are gathered to vertices
+ *     with the screen barycentrics of the fragment's pixel centre.
+ *   MER_INTERIOR: derivative of each covered pixel's shaded value with the
+ *     index image fixed (Eq. 5 second term).
+ * grad_vpix [n,V,3] float32 (+=): dL/d(x_s, y_s, zeta) per view.
+ * grad_attr [V,C_attr] (+=) or NULL: dL/d(attr) of the interior term. */
+int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
+                 const int32_t* index, const float* image, const float* grad_image,
+                 const float* attr, const float* tex, const mer_shading* shading_host, int terms,
+                 float* grad_vpix, float* grad_attr, void* status_ws, void* stream);
+
+/* EdgeGrad module backward alone (Supp. B): mer_backward with terms =
+ * MER_EDGE | (intersections ? MER_INTERSECT : 0) for an image of C channels. */
+int mer_edge_grad_backward(const float* image, const float* grad_image, int C, const int32_t* index,
+                           const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
+                           int intersections, float* grad_vpix, void* status_ws, void* stream);
+
+/* Interpolation module backward alone (Supp. B): interior term of plain
+ * attribute interpolation, grad_out [n,H,W,C_attr] -> grad_attr [V,C_attr] (+=,
+ * or NULL) and grad_vpix [n,V,3] (+=). */
+int mer_interpolate_backward(const float* attr, int C_attr, const int32_t* tris, int T, const mer_vertex* vpix,
+                             int V, const int32_t* index, int n, int H, int W, const float* grad_out,
+                             float* grad_attr, float* grad_vpix, void* status_ws, void* stream);
+
+/* Vertex transform backward (Supp. B): grad_verts [V,3] (+=) = sum over views
+ * of R^T J^T grad_vpix with J = d(x_s, y_s, zeta)/d(X_c, Y_c, Z_c). */
+int mer_project_backward(int V, const mer_camera* cams, int n, const mer_vertex* vpix, const float* grad_vpix,
+                         float* grad_verts, void* stream);
+
+/* Synchronises `stream`, reads and clears the device status word of a
+ * workspace (or of a status buffer of at least 256 bytes passed as status_ws to
+ * the other calls).  Returns MER_OK, MER_EOVERFLOW or MER_ERANGE; *total_bins
+ * (if not NULL) receives the number of bin entries the last mer_rasterize
+ * needed, so an overflowing caller can size the workspace exactly. */
+int mer_sync_status(void* workspace, int64_t* total_bins, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MER_H */

@@ -293,6 +293,9 @@ static dual dscale(dual a, double c) { dual r; r.v = a.v * c; for (int k = 0; k 
  * u wraps, v clamps to the edge texels.  Value and derivatives through (u, v). */
 static void tex_bilinear(const float* tex, int TH, int TW, int nc, dual u, dual v, dual* out)
 {
+    /* non-finite or far-out coordinates (|u| or |v| >= 1024) sample at 0 */
+    if (!(fabs(u.v) < 1024.0)) u = dconst(0.0);
+    if (!(fabs(v.v) < 1024.0)) v = dconst(0.0);
     dual x = dsub(dscale(u, (double)TW), dconst(0.5));
     double x0 = floor(x.v);
     dual fx = dsub(x, dconst(x0));

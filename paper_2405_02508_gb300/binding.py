@@ -1,0 +1,193 @@
+"""ctypes binding of ``libmer.so``: one Python function per C entry point, same names.
+
+Argument marshalling only: tensors are passed as raw device pointers on the
+current PyTorch stream; every step of the computation runs in the library's
+CUDA kernels.  There is no CPU fallback: without the compiled library (or
+without a GPU) these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+MER_OK, MER_EINVAL, MER_ECUDA, MER_EOVERFLOW, MER_ERANGE = 0, 1, 2, 3, 4
+MER_EDGE, MER_INTERIOR, MER_INTERSECT = 1, 2, 4
+CAMERA_DOUBLES = 17   # mer_camera: R[9], t[3], fx, fy, cx, cy, znear
+VERTEX_FLOATS = 8     # mer_vertex: 32 bytes
+
+
+class MerError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {strerror(code)} (code {code})")
+        self.code = code
+
+
+class MerShading(ctypes.Structure):
+    _fields_ = [("n_main", ctypes.c_int), ("C", ctypes.c_int), ("uv_offset", ctypes.c_int),
+                ("mask_ch", ctypes.c_int), ("depth_ch", ctypes.c_int), ("C_attr", ctypes.c_int),
+                ("tex_h", ctypes.c_int), ("tex_w", ctypes.c_int)]
+
+
+# (name, argtypes, restype); P = pointer, I = int, Z = size_t, L = int64
+_P, _I, _Z, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_int64
+_SIGS = {
+    "mer_strerror": ([_I], ctypes.c_char_p),
+    "mer_version": ([], _I),
+    "mer_workspace_size": ([_I, _I, _I, _I, _I, _I, _L], _Z),
+    "mer_project": ([_P, _I, _P, _I, _P, _P], _I),
+    "mer_project_screen": ([_P, _I, _I, _P, _P], _I),
+    "mer_rasterize": ([_P, _I, _P, _I, _I, _I, _I, _I, _P, _Z, _P, _P, _P, _P], _I),
+    "mer_shade": ([_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(MerShading), _P, _P, _P], _I),
+    "mer_backward": ([_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P, ctypes.POINTER(MerShading), _I, _P, _P, _P,
+                      _P], _I),
+    "mer_edge_grad_backward": ([_P, _P, _I, _P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _P, _P], _I),
+    "mer_interpolate_backward": ([_P, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
+    "mer_project_backward": ([_I, _P, _I, _P, _P, _P, _P], _I),
+    "mer_sync_status": ([_P, ctypes.POINTER(ctypes.c_int64), _P], _I),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libmer.so (building it first if it is missing or stale and nvcc is available)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing:
+            try:
+                path = _build.build_lib()
+            except RuntimeError:
+                if not os.path.exists(path):
+                    raise
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmer.so is not built ({path}); run paper_2405_02508_gb300.build.build_lib()")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def strerror(code: int) -> str:
+    return lib().mer_strerror(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != MER_OK:
+        raise MerError(code, where)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libmer takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("libmer takes contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def shading_struct(sh, C_attr: int, tex: torch.Tensor | None) -> MerShading:
+    s = MerShading()
+    s.n_main, s.C, s.uv_offset, s.mask_ch, s.depth_ch = sh.n_main, sh.C, sh.uv_offset, sh.mask_ch, sh.depth_ch
+    s.C_attr = C_attr
+    s.tex_h, s.tex_w = (int(tex.shape[0]), int(tex.shape[1])) if tex is not None else (0, 0)
+    return s
+
+
+def cameras_tensor(cams: np.ndarray, device="cuda") -> torch.Tensor:
+    """Packed mer_camera records [n, 17] float64 on the device."""
+    a = np.ascontiguousarray(cams).view(np.float64).reshape(len(cams), CAMERA_DOUBLES)
+    return torch.from_numpy(a.copy()).to(device)
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+
+def mer_workspace_size(V: int, T: int, n: int, H: int, W: int, tile: int, bin_capacity: int = 0) -> int:
+    return int(lib().mer_workspace_size(V, T, n, H, W, tile, bin_capacity))
+
+
+def mer_project(verts: torch.Tensor, cams: torch.Tensor, vpix: torch.Tensor):
+    V, n = verts.shape[0], cams.shape[0]
+    _check(lib().mer_project(_ptr(verts), V, _ptr(cams), n, _ptr(vpix), _stream()), "mer_project")
+
+
+def mer_project_screen(scr: torch.Tensor, vpix: torch.Tensor):
+    n, V = scr.shape[0], scr.shape[1]
+    _check(lib().mer_project_screen(_ptr(scr), V, n, _ptr(vpix), _stream()), "mer_project_screen")
+
+
+def mer_rasterize(vpix, tris, H, W, tile, workspace, index, depth=None, bary=None):
+    n, V = vpix.shape[0], vpix.shape[1]
+    T = tris.shape[0]
+    _check(lib().mer_rasterize(_ptr(vpix), V, _ptr(tris), T, n, H, W, tile, _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _ptr(index), _ptr(depth), _ptr(bary),
+                               _stream()), "mer_rasterize")
+
+
+def mer_shade(vpix, tris, index, attr, tex, bg: np.ndarray, sh: MerShading, image, status_ws=None):
+    n, V = vpix.shape[0], vpix.shape[1]
+    H, W = index.shape[1], index.shape[2]
+    bgc = (ctypes.c_float * max(1, sh.C))(*[float(x) for x in bg])
+    _check(lib().mer_shade(_ptr(vpix), V, _ptr(tris), tris.shape[0], n, H, W, _ptr(index), _ptr(attr), _ptr(tex),
+                           ctypes.cast(bgc, ctypes.c_void_p), ctypes.byref(sh), _ptr(image), _ptr(status_ws),
+                           _stream()), "mer_shade")
+
+
+def mer_backward(vpix, tris, index, image, grad_image, attr, tex, sh: MerShading, terms: int, grad_vpix,
+                 grad_attr=None, status_ws=None):
+    n, V = vpix.shape[0], vpix.shape[1]
+    H, W = index.shape[1], index.shape[2]
+    _check(lib().mer_backward(_ptr(vpix), V, _ptr(tris), tris.shape[0], n, H, W, _ptr(index), _ptr(image),
+                              _ptr(grad_image), _ptr(attr), _ptr(tex), ctypes.byref(sh), terms, _ptr(grad_vpix),
+                              _ptr(grad_attr), _ptr(status_ws), _stream()), "mer_backward")
+
+
+def mer_edge_grad_backward(image, grad_image, index, vpix, tris, intersections: bool, grad_vpix, status_ws=None):
+    n, V = vpix.shape[0], vpix.shape[1]
+    H, W, C = image.shape[1], image.shape[2], image.shape[3]
+    _check(lib().mer_edge_grad_backward(_ptr(image), _ptr(grad_image), C, _ptr(index), _ptr(vpix), V, _ptr(tris),
+                                        tris.shape[0], n, H, W, int(bool(intersections)), _ptr(grad_vpix),
+                                        _ptr(status_ws), _stream()), "mer_edge_grad_backward")
+
+
+def mer_interpolate_backward(attr, tris, vpix, index, grad_out, grad_attr, grad_vpix, status_ws=None):
+    n, V = vpix.shape[0], vpix.shape[1]
+    H, W = index.shape[1], index.shape[2]
+    _check(lib().mer_interpolate_backward(_ptr(attr), attr.shape[1], _ptr(tris), tris.shape[0], _ptr(vpix), V,
+                                          _ptr(index), n, H, W, _ptr(grad_out), _ptr(grad_attr), _ptr(grad_vpix),
+                                          _ptr(status_ws), _stream()), "mer_interpolate_backward")
+
+
+def mer_project_backward(cams, vpix, grad_vpix, grad_verts):
+    n, V = vpix.shape[0], vpix.shape[1]
+    _check(lib().mer_project_backward(V, _ptr(cams), n, _ptr(vpix), _ptr(grad_vpix), _ptr(grad_verts), _stream()),
+           "mer_project_backward")
+
+
+def mer_sync_status(workspace) -> tuple[int, int]:
+    tot = ctypes.c_int64(0)
+    code = lib().mer_sync_status(_ptr(workspace), ctypes.byref(tot), _stream())
+    return code, int(tot.value)

@@ -1,0 +1,168 @@
+// abi.cu -- the extern "C" entry points of libmer.so declared in include/mer.h:
+// host-side argument validation, then the kernel launches of the other units.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mer_device.cuh"
+
+extern "C" int mer_launch_project(const float*, int, const mer_camera*, int, mer_vertex*, cudaStream_t);
+extern "C" int mer_launch_project_screen(const double*, int, int, mer_vertex*, cudaStream_t);
+extern "C" int mer_launch_project_backward(int, const mer_camera*, int, const mer_vertex*, const float*, float*,
+                                           cudaStream_t);
+extern "C" size_t mer_raster_workspace_size(int, int, int, int, int, int, long long);
+extern "C" int mer_launch_rasterize(const mer_vertex*, int, const int*, int, int, int, int, int, void*, size_t, int*,
+                                    float*, float*, cudaStream_t);
+extern "C" int mer_launch_shade(const mer_vertex*, int, const int*, int, int, int, int, const int*, const float*,
+                                const float*, const float*, const mer_shading*, float*, void*, cudaStream_t);
+extern "C" int mer_launch_backward(const mer_vertex*, int, const int*, int, int, int, int, const int*, const float*,
+                                   const float*, const float*, const float*, const mer_shading*, int, float*, float*,
+                                   void*, cudaStream_t);
+
+namespace {
+
+inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+inline bool dims_ok(int n, int H, int W) {
+    if (n < 0 || H < 0 || W < 0) return false;
+    if (H > mer::kMaxDim || W > mer::kMaxDim) return false;
+    return (long long)n * H * W < (1LL << 31);
+}
+
+inline bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
+bool shading_ok(const mer_shading* sh) {
+    if (!sh) return false;
+    if (sh->C < 1 || sh->C > mer::kMaxC) return false;
+    if (sh->n_main < 0 || sh->n_main > sh->C) return false;
+    if (sh->mask_ch >= sh->C || sh->depth_ch >= sh->C) return false;
+    if (sh->mask_ch >= 0 && sh->mask_ch < sh->n_main) return false;
+    if (sh->depth_ch >= 0 && sh->depth_ch < sh->n_main) return false;
+    if (sh->mask_ch >= 0 && sh->mask_ch == sh->depth_ch) return false;
+    if (sh->uv_offset >= 0) {
+        if (sh->uv_offset + 2 > sh->C_attr || sh->tex_h < 1 || sh->tex_w < 1) return false;
+    } else if (sh->n_main > sh->C_attr) {
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mer_strerror(int code) {
+    switch (code) {
+        case MER_OK: return "ok";
+        case MER_EINVAL: return "invalid argument";
+        case MER_ECUDA: return "CUDA error";
+        case MER_EOVERFLOW: return "bin list overflow: workspace too small";
+        case MER_ERANGE: return "triangle or index-image entry out of range";
+        default: return "unknown error";
+    }
+}
+
+int mer_version(void) { return 1; }
+
+size_t mer_workspace_size(int V, int T, int n, int H, int W, int tile, int64_t bin_capacity) {
+    if (V < 0 || T < 0 || !dims_ok(n, H, W) || (tile != 8 && tile != 16 && tile != 32)) return 0;
+    return mer_raster_workspace_size(V, T, n, H, W, tile, (long long)bin_capacity);
+}
+
+int mer_project(const float* verts, int V, const mer_camera* cams, int n, mer_vertex* vpix, void* stream) {
+    if (V < 0 || n < 0) return MER_EINVAL;
+    if ((long long)V * n == 0) return MER_OK;
+    if (!verts || !cams || !vpix) return MER_EINVAL;
+    return mer_launch_project(verts, V, cams, n, vpix, S(stream));
+}
+
+int mer_project_screen(const double* scr, int V, int n, mer_vertex* vpix, void* stream) {
+    if (V < 0 || n < 0) return MER_EINVAL;
+    if ((long long)V * n == 0) return MER_OK;
+    if (!scr || !vpix) return MER_EINVAL;
+    return mer_launch_project_screen(scr, V, n, vpix, S(stream));
+}
+
+int mer_rasterize(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W, int tile,
+                  void* workspace, size_t workspace_bytes, int32_t* index, float* depth, float* bary, void* stream) {
+    if (V < 0 || T < 0 || !dims_ok(n, H, W)) return MER_EINVAL;
+    if (tile != 8 && tile != 16 && tile != 32) return MER_EINVAL;
+    if ((long long)n * H * W == 0) return MER_OK;
+    if (!workspace || !aligned256(workspace) || !index) return MER_EINVAL;
+    if (T > 0 && (!tris || !vpix)) return MER_EINVAL;
+    if (workspace_bytes < mer_raster_workspace_size(V, T, n, H, W, tile, 1)) return MER_EINVAL;
+    return mer_launch_rasterize(vpix, V, tris, T, n, H, W, tile, workspace, workspace_bytes, index, depth, bary,
+                                S(stream));
+}
+
+int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W, const int32_t* index,
+              const float* attr, const float* tex, const float* bg_host, const mer_shading* sh, float* image,
+              void* status_ws, void* stream) {
+    if (V < 0 || T < 0 || !dims_ok(n, H, W) || !shading_ok(sh)) return MER_EINVAL;
+    if ((long long)n * H * W == 0) return MER_OK;
+    if (!index || !image) return MER_EINVAL;
+    if (T > 0 && (!tris || !vpix)) return MER_EINVAL;
+    if (sh->n_main > 0 && !attr) return MER_EINVAL;
+    if (sh->uv_offset >= 0 && !tex) return MER_EINVAL;
+    if (status_ws && !aligned256(status_ws)) return MER_EINVAL;
+    return mer_launch_shade(vpix, V, tris, T, n, H, W, index, attr, tex, bg_host, sh, image, status_ws, S(stream));
+}
+
+int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W, const int32_t* index,
+                 const float* image, const float* grad_image, const float* attr, const float* tex,
+                 const mer_shading* sh, int terms, float* grad_vpix, float* grad_attr, void* status_ws, void* stream) {
+    if (V < 0 || T < 0 || !dims_ok(n, H, W) || !shading_ok(sh)) return MER_EINVAL;
+    if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT)) return MER_EINVAL;
+    if ((long long)n * H * W == 0 || terms == 0) return MER_OK;
+    if (!index || !grad_image || !grad_vpix) return MER_EINVAL;
+    if (T > 0 && (!tris || !vpix)) return MER_EINVAL;
+    if ((terms & MER_EDGE) && !image) return MER_EINVAL;
+    if ((terms & MER_INTERIOR) && sh->n_main > 0 && !attr) return MER_EINVAL;
+    if ((terms & MER_INTERIOR) && sh->uv_offset >= 0 && !tex) return MER_EINVAL;
+    if (status_ws && !aligned256(status_ws)) return MER_EINVAL;
+    return mer_launch_backward(vpix, V, tris, T, n, H, W, index, image, grad_image, attr, tex, sh, terms, grad_vpix,
+                               grad_attr, status_ws, S(stream));
+}
+
+int mer_edge_grad_backward(const float* image, const float* grad_image, int C, const int32_t* index,
+                           const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
+                           int intersections, float* grad_vpix, void* status_ws, void* stream) {
+    mer_shading sh = {0, C, -1, -1, -1, 0, 0, 0};
+    return mer_backward(vpix, V, tris, T, n, H, W, index, image, grad_image, nullptr, nullptr, &sh,
+                        MER_EDGE | (intersections ? MER_INTERSECT : 0), grad_vpix, nullptr, status_ws, stream);
+}
+
+int mer_interpolate_backward(const float* attr, int C_attr, const int32_t* tris, int T, const mer_vertex* vpix, int V,
+                             const int32_t* index, int n, int H, int W, const float* grad_out, float* grad_attr,
+                             float* grad_vpix, void* status_ws, void* stream) {
+    mer_shading sh = {C_attr, C_attr, -1, -1, -1, C_attr, 0, 0};
+    return mer_backward(vpix, V, tris, T, n, H, W, index, nullptr, grad_out, attr, nullptr, &sh, MER_INTERIOR,
+                        grad_vpix, grad_attr, status_ws, stream);
+}
+
+int mer_project_backward(int V, const mer_camera* cams, int n, const mer_vertex* vpix, const float* grad_vpix,
+                         float* grad_verts, void* stream) {
+    if (V < 0 || n < 0) return MER_EINVAL;
+    if ((long long)V * n == 0) return MER_OK;
+    if (!cams || !vpix || !grad_vpix || !grad_verts) return MER_EINVAL;
+    return mer_launch_project_backward(V, cams, n, vpix, grad_vpix, grad_verts, S(stream));
+}
+
+int mer_sync_status(void* workspace, int64_t* total_bins, void* stream) {
+    if (!workspace || !aligned256(workspace)) return MER_EINVAL;
+    mer::WsHeader h;
+    if (cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, S(stream)) != cudaSuccess) return MER_ECUDA;
+    if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return MER_ECUDA;
+    if (total_bins) *total_bins = h.total_bins;
+    if (h.status != 0) {
+        const int zero = 0;
+        if (cudaMemcpyAsync(workspace, &zero, sizeof(int), cudaMemcpyHostToDevice, S(stream)) != cudaSuccess)
+            return MER_ECUDA;
+        if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return MER_ECUDA;
+    }
+    if (h.status & mer::kStatusOverflow) return MER_EOVERFLOW;
+    if (h.status & mer::kStatusRange) return MER_ERANGE;
+    return MER_OK;
+}
+
+}  // extern "C"

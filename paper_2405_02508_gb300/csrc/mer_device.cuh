@@ -1,0 +1,174 @@
+// mer_device.cuh -- device-side building blocks shared by the kernels of libmer.
+//
+// Exact coverage (snapped int64 edge functions with the top-left rule), the
+// FP32 depth key of the z-buffer, accurate screen barycentrics from the
+// snapped-plus-residual vertex records, and the bilinear texture sampler.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/mer.h"
+
+namespace mer {
+
+constexpr int kMaxDim = 8192;
+constexpr double kGuard = 536870912.0;  // 2^29 (snapped units)
+constexpr uint32_t kValid = 3u;         // in front of the near plane and inside the guard band
+constexpr int kMaxC = 16;               // channels of a shaded image handled per pixel
+
+// Workspace header, first 256 bytes of every workspace / status buffer.
+struct WsHeader {
+    int status;          // bit 0: bin overflow, bit 1: triangle / index out of range
+    int pad0;
+    long long total_bins;
+    long long capacity;
+    int pad[58];
+};
+static_assert(sizeof(WsHeader) == 256, "header");
+constexpr int kStatusOverflow = 1;
+constexpr int kStatusRange = 2;
+
+// Per (view, triangle) raster record written by the binning pass, 48 bytes.
+struct TriRaster {
+    int X[3], Y[3];   // snapped vertex positions
+    float zd[3];      // zeta_i / (E_0 + E_1 + E_2), FP32
+    int flags;        // bits 0..2: edge i is top-left; bit 3: negative area; bit 31: culled
+    short bx0, bx1, by0, by1;  // inclusive pixel bounding box of the covered centres
+};
+static_assert(sizeof(TriRaster) == 48, "TriRaster");
+
+__device__ __forceinline__ int64_t edge_fn(int xj, int yj, int xk, int yk, int px, int py) {
+    // cross(v_j - P, v_k - P); every factor fits int32 (|X| <= 2^29, P < 2^22)
+    return (int64_t)(xj - px) * (int64_t)(yk - py) - (int64_t)(yj - py) * (int64_t)(xk - px);
+}
+
+// Exact coverage of the pixel centre (px, py) (snapped units) by a raster record.
+__device__ __forceinline__ bool covers(const TriRaster& t, int px, int py, int64_t E[3]) {
+    const bool neg = (t.flags & 8) != 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, k = (i + 2) % 3;
+        int64_t e = edge_fn(t.X[j], t.Y[j], t.X[k], t.Y[k], px, py);
+        E[i] = e;
+        if (neg) e = -e;
+        // covered iff e > 0, or e == 0 on a top-left edge: e + tl > 0
+        if (e + (int64_t)((t.flags >> i) & 1) <= 0) return false;
+    }
+    return true;
+}
+
+// Same predicate from three vertex records (used by the classification).
+__device__ __forceinline__ bool covers_pts(const int X[3], const int Y[3], int px, int py) {
+    const int64_t a2 = (int64_t)(X[1] - X[0]) * (Y[2] - Y[0]) - (int64_t)(Y[1] - Y[0]) * (X[2] - X[0]);
+    if (a2 == 0) return false;
+    const int64_t s = a2 > 0 ? 1 : -1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, k = (i + 2) % 3;
+        const int64_t e = s * edge_fn(X[j], Y[j], X[k], Y[k], px, py);
+        if (e > 0) continue;
+        if (e < 0) return false;
+        const int64_t ga = s * (int64_t)(Y[j] - Y[k]);
+        const int64_t gb = s * (int64_t)(X[k] - X[j]);
+        if (!(ga > 0 || (ga == 0 && gb > 0))) return false;
+    }
+    return true;
+}
+
+// FP32 depth key: sum_i E_i * (zeta_i / sum E) with correctly rounded conversions
+// and an FMA chain (relative error <= 7 * 2^-24, see the design notes).
+__device__ __forceinline__ float depth_key(const TriRaster& t, const int64_t E[3]) {
+    float z = __fmul_rn(__ll2float_rn(E[0]), t.zd[0]);
+    z = __fmaf_rn(__ll2float_rn(E[1]), t.zd[1], z);
+    z = __fmaf_rn(__ll2float_rn(E[2]), t.zd[2], z);
+    return z;
+}
+
+// a*d - b*c with one rounding error less (Kahan's product difference, FMA based).
+__device__ __forceinline__ float diff_of_products(float a, float d, float b, float c) {
+    const float w = b * c;
+    const float e = __fmaf_rn(-b, c, w);
+    const float f = __fmaf_rn(a, d, -w);
+    return f + e;
+}
+
+// Unsnapped position of a vertex relative to the pixel centre (px, py) in pixels.
+// The integer part is exact; the residual adds one rounding.
+__device__ __forceinline__ void rel_pos(const mer_vertex& v, int pxf, int pyf, float& dx, float& dy) {
+    dx = __fadd_rn(__int2float_rn(v.X - pxf) * (1.0f / 256.0f), v.rx);
+    dy = __fadd_rn(__int2float_rn(v.Y - pyf) * (1.0f / 256.0f), v.ry);
+}
+
+// Screen barycentrics of a pixel centre and their screen gradients.
+struct Bary {
+    float lam[3];
+    float gx[3], gy[3];  // d lambda_i / d P_x, d lambda_i / d P_y
+    float d;             // twice the signed area
+};
+
+__device__ __forceinline__ Bary screen_bary(const mer_vertex* v[3], int x, int y) {
+    const int pxf = 256 * x + 128, pyf = 256 * y + 128;
+    float dx[3], dy[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) rel_pos(*v[i], pxf, pyf, dx[i], dy[i]);
+    Bary b;
+    float e[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, k = (i + 2) % 3;
+        e[i] = diff_of_products(dx[j], dy[k], dy[j], dx[k]);
+    }
+    b.d = (e[0] + e[1]) + e[2];
+    const float inv = 1.0f / b.d;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, k = (i + 2) % 3;
+        b.lam[i] = e[i] * inv;
+        b.gx[i] = (dy[j] - dy[k]) * inv;
+        b.gy[i] = (dx[k] - dx[j]) * inv;
+    }
+    return b;
+}
+
+// Bilinear texture sample (u wraps, v clamps), value and d/du, d/dv per channel.
+__device__ __forceinline__ void tex_sample(const float* __restrict__ tex, int TH, int TW, int nc, float u, float v,
+                                           float* val, float* du, float* dv) {
+    // non-finite or far-out coordinates sample at 0 (keeps every index exact and in range)
+    if (!(fabsf(u) < 1024.0f)) u = 0.0f;
+    if (!(fabsf(v) < 1024.0f)) v = 0.0f;
+    const float x = u * (float)TW - 0.5f;
+    const float x0f = floorf(x);
+    const float fx = x - x0f;
+    int i0 = (int)(x0f - floorf(x0f / (float)TW) * (float)TW);
+    if (i0 < 0) i0 += TW;
+    if (i0 >= TW) i0 -= TW;
+    i0 = min(max(i0, 0), TW - 1);
+    const int i1 = (i0 + 1 == TW) ? 0 : i0 + 1;
+    float y = v * (float)TH - 0.5f;
+    bool clamped = false;
+    if (y < 0.0f) { y = 0.0f; clamped = true; }
+    if (y > (float)(TH - 1)) { y = (float)(TH - 1); clamped = true; }
+    const float y0f = floorf(y);
+    const float fy = y - y0f;
+    const int j0 = (int)y0f;
+    const int j1 = j0 + 1 < TH ? j0 + 1 : TH - 1;
+    const float* r0 = tex + (size_t)j0 * TW * nc;
+    const float* r1 = tex + (size_t)j1 * TW * nc;
+    for (int c = 0; c < nc; ++c) {
+        const float t00 = __ldg(r0 + (size_t)i0 * nc + c), t10 = __ldg(r0 + (size_t)i1 * nc + c);
+        const float t01 = __ldg(r1 + (size_t)i0 * nc + c), t11 = __ldg(r1 + (size_t)i1 * nc + c);
+        const float a = t00 + fx * (t10 - t00);
+        const float b = t01 + fx * (t11 - t01);
+        val[c] = a + fy * (b - a);
+        if (du) {
+            du[c] = (float)TW * ((1.0f - fy) * (t10 - t00) + fy * (t11 - t01));
+            dv[c] = clamped ? 0.0f : (float)TH * (b - a);
+        }
+    }
+}
+
+__device__ __forceinline__ void set_status(void* ws, int bit) {
+    if (ws) atomicOr(&reinterpret_cast<WsHeader*>(ws)->status, bit);
+}
+
+}  // namespace mer

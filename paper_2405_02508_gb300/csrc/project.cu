@@ -1,0 +1,114 @@
+// project.cu -- vertex transform module (Supp. B) and its backward.
+//
+// Forward in FP64 with a fixed operation order and correctly rounded intrinsics
+// (no contraction into FMA), so the snapped screen positions X = rint(256 x_s)
+// are reproducible bit for bit by any IEEE FP64 implementation of the same
+// formula.  Backward in FP32.
+#include <cuda_runtime.h>
+
+#include "mer_device.cuh"
+
+namespace mer {
+
+__device__ __forceinline__ void write_vertex(double xs, double ys, double zeta, bool front, mer_vertex* out) {
+    mer_vertex r;
+    r.X = 0; r.Y = 0; r.rx = 0.f; r.ry = 0.f; r.zeta = 0.f; r.zeta_lo = 0.f; r.flags = 0u; r.pad = 0.f;
+    if (front) {
+        r.flags = 1u;
+        const double X = __dmul_rn(xs, 256.0), Y = __dmul_rn(ys, 256.0);  // exact (power of two)
+        if (fabs(X) <= kGuard && fabs(Y) <= kGuard) {
+            r.flags |= 2u;
+            const long long sx = __double2ll_rn(X), sy = __double2ll_rn(Y);  // ties to even
+            r.X = (int)sx;
+            r.Y = (int)sy;
+            r.rx = __double2float_rn(__dsub_rn(xs, __dmul_rn((double)sx, 1.0 / 256.0)));
+            r.ry = __double2float_rn(__dsub_rn(ys, __dmul_rn((double)sy, 1.0 / 256.0)));
+        }
+        r.zeta = __double2float_rn(zeta);
+        r.zeta_lo = __double2float_rn(__dsub_rn(zeta, (double)r.zeta));
+    }
+    *out = r;
+}
+
+__global__ void k_project(const float* __restrict__ verts, int V, const mer_camera* __restrict__ cams, int n,
+                          mer_vertex* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)V * n) return;
+    const int view = (int)(i / V), v = (int)(i % V);
+    const mer_camera& c = cams[view];
+    const double x = verts[3 * (size_t)v], y = verts[3 * (size_t)v + 1], z = verts[3 * (size_t)v + 2];
+    const double* R = c.R;
+    const double Xc = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(R[0], x), __dmul_rn(R[1], y)), __dmul_rn(R[2], z)), c.t[0]);
+    const double Yc = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(R[3], x), __dmul_rn(R[4], y)), __dmul_rn(R[5], z)), c.t[1]);
+    const double Zc = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(R[6], x), __dmul_rn(R[7], y)), __dmul_rn(R[8], z)), c.t[2]);
+    const bool front = Zc > c.znear;
+    double zeta = 0.0, xs = 0.0, ys = 0.0;
+    if (front) {
+        zeta = __drcp_rn(Zc);
+        xs = __dadd_rn(__dmul_rn(__dmul_rn(c.fx, Xc), zeta), c.cx);
+        ys = __dadd_rn(__dmul_rn(__dmul_rn(c.fy, Yc), zeta), c.cy);
+    }
+    write_vertex(xs, ys, zeta, front, out + i);
+}
+
+__global__ void k_project_screen(const double* __restrict__ scr, int V, int n, mer_vertex* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)V * n) return;
+    const double xs = scr[3 * i], ys = scr[3 * i + 1], zeta = scr[3 * i + 2];
+    write_vertex(xs, ys, zeta, zeta > 0.0, out + i);
+}
+
+// One thread per vertex, looping over the views: grad_world = sum_views R^T J^T g,
+// J = d(x_s, y_s, zeta)/d(X_c, Y_c, Z_c) = [[fx z, 0, -(x_s-cx) z], [0, fy z, -(y_s-cy) z], [0, 0, -z^2]].
+__global__ void k_project_backward(int V, const mer_camera* __restrict__ cams, int n,
+                                   const mer_vertex* __restrict__ vpix, const float* __restrict__ grad_vpix,
+                                   float* __restrict__ grad_verts) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int view = 0; view < n; ++view) {
+        const size_t k = (size_t)view * V + v;
+        const mer_vertex r = vpix[k];
+        if ((r.flags & 1u) == 0u) continue;
+        const mer_camera& c = cams[view];
+        const float gx = grad_vpix[3 * k], gy = grad_vpix[3 * k + 1], gz = grad_vpix[3 * k + 2];
+        const float z = r.zeta;
+        const float xs = (float)((double)r.X * (1.0 / 256.0) - c.cx) + r.rx;
+        const float ys = (float)((double)r.Y * (1.0 / 256.0) - c.cy) + r.ry;
+        const float gX = gx * (float)c.fx * z;
+        const float gY = gy * (float)c.fy * z;
+        const float gZ = -z * (gx * xs + gy * ys + gz * z);
+        a0 += (float)c.R[0] * gX + (float)c.R[3] * gY + (float)c.R[6] * gZ;
+        a1 += (float)c.R[1] * gX + (float)c.R[4] * gY + (float)c.R[7] * gZ;
+        a2 += (float)c.R[2] * gX + (float)c.R[5] * gY + (float)c.R[8] * gZ;
+    }
+    grad_verts[3 * (size_t)v] += a0;
+    grad_verts[3 * (size_t)v + 1] += a1;
+    grad_verts[3 * (size_t)v + 2] += a2;
+}
+
+}  // namespace mer
+
+using namespace mer;
+
+extern "C" int mer_launch_project(const float* verts, int V, const mer_camera* cams, int n, mer_vertex* vpix,
+                                  cudaStream_t s) {
+    const long long N = (long long)V * n;
+    if (N == 0) return 0;
+    k_project<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(verts, V, cams, n, vpix);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+extern "C" int mer_launch_project_screen(const double* scr, int V, int n, mer_vertex* vpix, cudaStream_t s) {
+    const long long N = (long long)V * n;
+    if (N == 0) return 0;
+    k_project_screen<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(scr, V, n, vpix);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+extern "C" int mer_launch_project_backward(int V, const mer_camera* cams, int n, const mer_vertex* vpix,
+                                           const float* grad_vpix, float* grad_verts, cudaStream_t s) {
+    if (V == 0 || n == 0) return 0;
+    k_project_backward<<<(V + 255) / 256, 256, 0, s>>>(V, cams, n, vpix, grad_vpix, grad_verts);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}

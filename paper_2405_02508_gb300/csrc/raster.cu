@@ -1,0 +1,345 @@
+// raster.cu -- rasterization module with z-buffer (Supp. B): triangle setup and
+// tile binning, then a per-tile raster that stages the tile's triangle records in
+// shared memory and keeps each pixel's nearest fragment in registers.
+//
+// Pipeline per call (all views of one mesh at once):
+//   k_setup_count : per (view, triangle): cull, exact setup record, pixel bbox,
+//                   count the bin tiles it overlaps
+//   k_scan_*      : exclusive scan of the per-tile counts -> list offsets
+//   k_bin_fill    : scatter triangle ids into the per-tile lists
+//   k_raster<TS>  : one CTA per (view, tile): coverage + depth test, write
+//                   index / depth / bary
+#include <cuda_runtime.h>
+
+#include "mer_device.cuh"
+
+namespace mer {
+
+struct BinGeom {
+    int n, H, W, T, V, tile, ntx, nty;
+    long long tiles_per_view;
+};
+
+__device__ __forceinline__ int floordiv256(int a) { return a >> 8; }  // arithmetic shift = floor
+
+// Pixel bbox of the centres (256x+128) inside [mn, mx] (snapped units), clamped to [0, lim-1].
+__device__ __forceinline__ void centre_range(int mn, int mx, int lim, int& lo, int& hi) {
+    // x >= ceil((mn - 128) / 256), x <= floor((mx - 128) / 256)
+    lo = -floordiv256(-(mn - 128));
+    hi = floordiv256(mx - 128);
+    lo = max(lo, 0);
+    hi = min(hi, lim - 1);
+}
+
+__global__ void k_setup_count(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris, BinGeom g,
+                              TriRaster* __restrict__ recs, int* __restrict__ counts, void* ws) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)g.T * g.n) return;
+    const int view = (int)(i / g.T), t = (int)(i % g.T);
+    TriRaster r;
+    r.flags = (int)0x80000000;  // culled unless set up below
+    r.bx0 = 1; r.bx1 = 0; r.by0 = 1; r.by1 = 0;
+    int vid[3];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        vid[k] = tris[3 * (size_t)t + k];
+        if (vid[k] < 0 || vid[k] >= g.V) ok = false;
+    }
+    if (!ok) {
+        set_status(ws, kStatusRange);
+        recs[i] = r;
+        return;
+    }
+    const mer_vertex* vb = vpix + (size_t)view * g.V;
+    mer_vertex v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v[k] = vb[vid[k]];
+        if ((v[k].flags & kValid) != kValid) ok = false;
+        r.X[k] = v[k].X;
+        r.Y[k] = v[k].Y;
+    }
+    if (!ok) { recs[i] = r; return; }
+    const int64_t a2 = (int64_t)(r.X[1] - r.X[0]) * (r.Y[2] - r.Y[0]) - (int64_t)(r.Y[1] - r.Y[0]) * (r.X[2] - r.X[0]);
+    if (a2 == 0) { recs[i] = r; return; }
+    const int mnx = min(r.X[0], min(r.X[1], r.X[2])), mxx = max(r.X[0], max(r.X[1], r.X[2]));
+    const int mny = min(r.Y[0], min(r.Y[1], r.Y[2])), mxy = max(r.Y[0], max(r.Y[1], r.Y[2]));
+    int x0, x1, y0, y1;
+    centre_range(mnx, mxx, g.W, x0, x1);
+    centre_range(mny, mxy, g.H, y0, y1);
+    if (x0 > x1 || y0 > y1) { recs[i] = r; return; }
+    const int s = a2 > 0 ? 1 : -1;
+    int fl = a2 > 0 ? 0 : 8;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int j = (e + 1) % 3, k = (e + 2) % 3;
+        const int64_t ga = (int64_t)s * (r.Y[j] - r.Y[k]);
+        const int64_t gb = (int64_t)s * (r.X[k] - r.X[j]);
+        if (ga > 0 || (ga == 0 && gb > 0)) fl |= 1 << e;
+    }
+    r.flags = fl;
+    const float Df = __ll2float_rn(a2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.zd[k] = __fdiv_rn(v[k].zeta, Df);
+    r.bx0 = (short)x0; r.bx1 = (short)x1; r.by0 = (short)y0; r.by1 = (short)y1;
+    recs[i] = r;
+    int* cnt = counts + (size_t)view * g.tiles_per_view;
+    for (int ty = y0 / g.tile; ty <= y1 / g.tile; ++ty)
+        for (int tx = x0 / g.tile; tx <= x1 / g.tile; ++tx) atomicAdd(cnt + ty * g.ntx + tx, 1);
+}
+
+// --- exclusive scan of the tile counts (3 kernels, 1024 elements per block) ---
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    total = sh[(blockDim.x >> 5) - 1];
+    const int before = warp > 0 ? sh[warp - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void k_scan_blocks(const int* __restrict__ in, long long N, int* __restrict__ out, int* __restrict__ sums) {
+    __shared__ int sh[32];
+    const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+    const int v = i < N ? in[i] : 0;
+    int total;
+    const int ex = block_exclusive_scan(v, sh, total);
+    if (i < N) out[i] = ex;
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// Single CTA: exclusive scan of the block sums (looping), total written to the header.
+__global__ void k_scan_sums(int* __restrict__ sums, int nb, void* ws, long long capacity) {
+    __shared__ int sh[32];
+    int carry = 0;
+    for (int base = 0; base < nb; base += kScanBlock) {
+        const int i = base + threadIdx.x;
+        const int v = i < nb ? sums[i] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, sh, total);
+        if (i < nb) sums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) {
+        WsHeader* h = reinterpret_cast<WsHeader*>(ws);
+        h->total_bins = carry;
+        h->capacity = capacity;
+        if (carry > capacity) atomicOr(&h->status, kStatusOverflow);
+    }
+}
+
+__global__ void k_scan_add(int* __restrict__ out, long long N, const int* __restrict__ sums, int* __restrict__ cursor) {
+    const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+    if (i < N) {
+        out[i] += sums[blockIdx.x];
+        cursor[i] = 0;
+    }
+}
+
+__global__ void k_bin_fill(const TriRaster* __restrict__ recs, BinGeom g, const int* __restrict__ offs,
+                           int* __restrict__ cursor, int* __restrict__ list, long long capacity) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)g.T * g.n) return;
+    const TriRaster& r = recs[i];
+    if (r.flags < 0) return;
+    const int view = (int)(i / g.T), t = (int)(i % g.T);
+    const size_t base = (size_t)view * g.tiles_per_view;
+    for (int ty = r.by0 / g.tile; ty <= r.by1 / g.tile; ++ty)
+        for (int tx = r.bx0 / g.tile; tx <= r.bx1 / g.tile; ++tx) {
+            const size_t tile = base + (size_t)ty * g.ntx + tx;
+            const long long pos = (long long)offs[tile] + atomicAdd(cursor + tile, 1);
+            if (pos < capacity) list[pos] = t;
+        }
+}
+
+// --- raster ---
+constexpr int kStage = 256;  // triangle records staged per round
+
+template <int TS>
+struct RasterCfg {
+    static constexpr int threads = TS * TS < 256 ? TS * TS : 256;
+    static constexpr int ppt = TS * TS / threads;  // pixels per thread
+};
+
+template <int TS>
+__global__ void __launch_bounds__(RasterCfg<TS>::threads) k_raster(const TriRaster* __restrict__ recs, BinGeom g,
+                                                           const int* __restrict__ offs, const int* __restrict__ cnts,
+                                                           const int* __restrict__ list, const mer_vertex* __restrict__ vpix,
+                                                           const int* __restrict__ tris, void* ws, long long capacity,
+                                                           int* __restrict__ index, float* __restrict__ depth,
+                                                           float* __restrict__ bary) {
+    constexpr int kRasterThreads = RasterCfg<TS>::threads;
+    constexpr int PPT = RasterCfg<TS>::ppt;
+    __shared__ TriRaster sh[kStage];
+    __shared__ int sh_id[kStage];
+    const WsHeader* hdr = reinterpret_cast<const WsHeader*>(ws);
+    const bool overflow = hdr->total_bins > capacity;
+    const long long tile = blockIdx.x;
+    const int view = (int)(tile / g.tiles_per_view);
+    const int local = (int)(tile % g.tiles_per_view);
+    const int ty = local / g.ntx, tx = local % g.ntx;
+    int px[PPT], py[PPT];
+    float bz[PPT];
+    int bid[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int p = threadIdx.x + k * kRasterThreads;
+        px[k] = tx * TS + (p % TS);
+        py[k] = ty * TS + (p / TS);
+        bz[k] = -1.0f;
+        bid[k] = -1;
+    }
+    const int count = overflow ? 0 : cnts[tile];
+    const int off = overflow ? 0 : offs[tile];
+    const TriRaster* rv = recs + (size_t)view * g.T;
+    for (int base = 0; base < count; base += kStage) {
+        const int m = min(kStage, count - base);
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += kRasterThreads) {
+            const int t = list[off + base + j];
+            sh[j] = rv[t];
+            sh_id[j] = t;
+        }
+        __syncthreads();
+        for (int j = 0; j < m; ++j) {
+            const TriRaster& r = sh[j];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (px[k] < r.bx0 || px[k] > r.bx1 || py[k] < r.by0 || py[k] > r.by1) continue;
+                int64_t E[3];
+                if (!covers(r, 256 * px[k] + 128, 256 * py[k] + 128, E)) continue;
+                const float z = depth_key(r, E);
+                const int id = sh_id[j];
+                if (z > bz[k] || (z == bz[k] && id < bid[k])) {
+                    bz[k] = z;
+                    bid[k] = id;
+                }
+            }
+        }
+    }
+    const mer_vertex* vb = vpix + (size_t)view * g.V;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (px[k] >= g.W || py[k] >= g.H) continue;
+        const size_t p = ((size_t)view * g.H + py[k]) * g.W + px[k];
+        const int t = bid[k];
+        index[p] = t;
+        if (!depth && !bary) continue;
+        float Z = 0.f, b1 = 0.f, b2 = 0.f;
+        if (t >= 0) {
+            const mer_vertex* v[3] = {vb + tris[3 * (size_t)t], vb + tris[3 * (size_t)t + 1], vb + tris[3 * (size_t)t + 2]};
+            const Bary B = screen_bary(v, px[k], py[k]);
+            const float z0 = v[0]->zeta, z1 = v[1]->zeta, z2 = v[2]->zeta;
+            const float s = B.lam[0] * z0 + B.lam[1] * z1 + B.lam[2] * z2;
+            const float is = 1.0f / s;
+            Z = is;
+            b1 = B.lam[1] * z1 * is;
+            b2 = B.lam[2] * z2 * is;
+        }
+        if (depth) depth[p] = Z;
+        if (bary) {
+            bary[2 * p] = b1;
+            bary[2 * p + 1] = b2;
+        }
+    }
+}
+
+}  // namespace mer
+
+using namespace mer;
+
+namespace {
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+}
+
+struct RasterLayout {
+    size_t hdr, counts, offs, cursor, sums, recs, list, total;
+    long long ntiles, nblocks, capacity;
+};
+
+static RasterLayout raster_layout(int V, int T, int n, int H, int W, int tile, long long capacity) {
+    (void)V;
+    RasterLayout L;
+    const long long ntx = (W + tile - 1) / tile, nty = (H + tile - 1) / tile;
+    L.ntiles = ntx * nty * (long long)n;
+    L.nblocks = (L.ntiles + kScanBlock - 1) / kScanBlock;
+    if (capacity <= 0) capacity = 4LL * n * T + 2LL * L.ntiles + 1024;
+    L.capacity = capacity;
+    size_t o = 0;
+    L.hdr = o; o += align256(sizeof(WsHeader));
+    L.counts = o; o += align256((size_t)L.ntiles * 4);
+    L.offs = o; o += align256((size_t)L.ntiles * 4);
+    L.cursor = o; o += align256((size_t)L.ntiles * 4);
+    L.sums = o; o += align256((size_t)(L.nblocks + 1) * 4);
+    L.recs = o; o += align256((size_t)n * T * sizeof(TriRaster));
+    L.list = o; o += align256((size_t)capacity * 4);
+    L.total = o;
+    return L;
+}
+
+extern "C" size_t mer_raster_workspace_size(int V, int T, int n, int H, int W, int tile, long long capacity) {
+    return raster_layout(V, T, n, H, W, tile, capacity).total;
+}
+
+extern "C" int mer_launch_rasterize(const mer_vertex* vpix, int V, const int* tris, int T, int n, int H, int W,
+                                    int tile, void* ws, size_t ws_bytes, int* index, float* depth, float* bary,
+                                    cudaStream_t s) {
+    // capacity: whatever the workspace holds beyond the fixed part
+    RasterLayout L = raster_layout(V, T, n, H, W, tile, 1);
+    if (ws_bytes < L.total) return 1;
+    const long long capacity = (long long)((ws_bytes - L.list) / 4);
+    L = raster_layout(V, T, n, H, W, tile, capacity);
+    char* base = static_cast<char*>(ws);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
+    int* counts = reinterpret_cast<int*>(base + L.counts);
+    int* offs = reinterpret_cast<int*>(base + L.offs);
+    int* cursor = reinterpret_cast<int*>(base + L.cursor);
+    int* sums = reinterpret_cast<int*>(base + L.sums);
+    TriRaster* recs = reinterpret_cast<TriRaster*>(base + L.recs);
+    int* list = reinterpret_cast<int*>(base + L.list);
+    BinGeom g;
+    g.n = n; g.H = H; g.W = W; g.T = T; g.V = V; g.tile = tile;
+    g.ntx = (W + tile - 1) / tile;
+    g.nty = (H + tile - 1) / tile;
+    g.tiles_per_view = (long long)g.ntx * g.nty;
+    // header: the status word is sticky until mer_sync_status; k_scan_sums writes the totals
+    if (cudaMemsetAsync(counts, 0, (size_t)L.ntiles * 4, s) != cudaSuccess) return 2;
+    const long long NT = (long long)T * n;
+    if (NT > 0) {
+        k_setup_count<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(vpix, tris, g, recs, counts, hdr);
+    }
+    k_scan_blocks<<<(unsigned)L.nblocks, kScanBlock, 0, s>>>(counts, L.ntiles, offs, sums);
+    k_scan_sums<<<1, kScanBlock, 0, s>>>(sums, (int)L.nblocks, hdr, capacity);
+    k_scan_add<<<(unsigned)L.nblocks, kScanBlock, 0, s>>>(offs, L.ntiles, sums, cursor);
+    if (NT > 0) {
+        k_bin_fill<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(recs, g, offs, cursor, list, capacity);
+    }
+    const unsigned grid = (unsigned)L.ntiles;
+    switch (tile) {
+        case 8: k_raster<8><<<grid, RasterCfg<8>::threads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
+        case 16: k_raster<16><<<grid, RasterCfg<16>::threads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
+        case 32: k_raster<32><<<grid, RasterCfg<32>::threads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
+        default: return 1;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}

@@ -1,0 +1,88 @@
+// shade.cu -- barycentrics + interpolation modules and deferred shading (Supp. B).
+//
+// One thread per pixel: re-derive the screen barycentrics of the pixel centre
+// from the index image and the projected vertex records, make them perspective
+// correct, and write the shaded channels (interpolated attributes or bilinear
+// texture, coverage mask, depth) as one contiguous NHWC run per pixel.
+#include <cuda_runtime.h>
+
+#include "mer_device.cuh"
+
+namespace mer {
+
+struct ShadeArgs {
+    mer_shading sh;
+    float bg[kMaxC];
+};
+
+__global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* __restrict__ tris, int T, int n, int H,
+                        int W, const int* __restrict__ index, const float* __restrict__ attr,
+                        const float* __restrict__ tex, ShadeArgs a, float* __restrict__ image, void* ws) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long npix = (long long)n * H * W;
+    if (p >= npix) return;
+    const int C = a.sh.C;
+    float out[kMaxC];
+#pragma unroll
+    for (int c = 0; c < kMaxC; ++c) out[c] = c < C ? a.bg[c] : 0.f;
+    const int t = index[p];
+    if (t >= T) set_status(ws, kStatusRange);
+    if (t >= 0 && t < T) {
+        const int view = (int)(p / ((long long)H * W));
+        const int rem = (int)(p % ((long long)H * W));
+        const int y = rem / W, x = rem % W;
+        const mer_vertex* vb = vpix + (size_t)view * V;
+        const int i0 = tris[3 * (size_t)t], i1 = tris[3 * (size_t)t + 1], i2 = tris[3 * (size_t)t + 2];
+        if ((unsigned)i0 >= (unsigned)V || (unsigned)i1 >= (unsigned)V || (unsigned)i2 >= (unsigned)V) {
+            set_status(ws, kStatusRange);
+            return;
+        }
+        const mer_vertex* v[3] = {vb + i0, vb + i1, vb + i2};
+        const int vid[3] = {i0, i1, i2};
+        const Bary B = screen_bary(v, x, y);
+        float b[3];
+        const float s = B.lam[0] * v[0]->zeta + B.lam[1] * v[1]->zeta + B.lam[2] * v[2]->zeta;
+        const float is = 1.0f / s;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b[k] = B.lam[k] * v[k]->zeta * is;
+        const int Ca = a.sh.C_attr;
+        if (a.sh.uv_offset < 0) {
+            for (int c = 0; c < a.sh.n_main; ++c) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) acc += b[k] * __ldg(attr + (size_t)vid[k] * Ca + c);
+                out[c] = acc;
+            }
+        } else {
+            float u = 0.f, w = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                u += b[k] * __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset);
+                w += b[k] * __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1);
+            }
+            tex_sample(tex, a.sh.tex_h, a.sh.tex_w, a.sh.n_main, u, w, out, nullptr, nullptr);
+        }
+        if (a.sh.mask_ch >= 0) out[a.sh.mask_ch] = 1.0f;
+        if (a.sh.depth_ch >= 0) out[a.sh.depth_ch] = is;
+    }
+    float* o = image + (size_t)p * C;
+#pragma unroll
+    for (int c = 0; c < kMaxC; ++c)
+        if (c < C) o[c] = out[c];
+}
+
+}  // namespace mer
+
+using namespace mer;
+
+extern "C" int mer_launch_shade(const mer_vertex* vpix, int V, const int* tris, int T, int n, int H, int W,
+                                const int* index, const float* attr, const float* tex, const float* bg,
+                                const mer_shading* sh, float* image, void* ws, cudaStream_t s) {
+    const long long npix = (long long)n * H * W;
+    if (npix == 0) return 0;
+    ShadeArgs a;
+    a.sh = *sh;
+    for (int c = 0; c < kMaxC; ++c) a.bg[c] = (bg && c < sh->C) ? bg[c] : 0.f;
+    k_shade<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(vpix, V, tris, T, n, H, W, index, attr, tex, a, image, ws);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}

@@ -1,0 +1,340 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle, element by element.
+
+The tolerances are stated in ``tests/parity.py``.  Scenes are the five workloads
+(tiny icosphere, interpenetrating spheres, head-scale single view, 32-view
+multi-view at full size with sampled oracle views, uneven batch items) plus
+edge cases: empty meshes, ragged and degenerate image sizes, all-background
+views, triangles behind the camera or far outside the image, and every bin
+tile size.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_2405_02508_gb300 import scenes
+from paper_2405_02508_gb300.scenes import Scene, Shading
+
+from . import parity
+
+pytestmark = pytest.mark.gpu
+
+ALL = 7
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+
+    oracle.build()
+    return oracle
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_2405_02508_gb300 import binding
+
+    binding.lib()
+
+
+def run_parity(orc, scene, grads, views=None, terms=ALL, tile=16, check_world=True, want_attr=False,
+               store_bary=True):
+    gpu = parity.gpu_run(scene, grads, terms=terms, tile=tile, want_attr=want_attr, store_bary=store_bary)
+    views = list(range(scene.n_views)) if views is None else list(views)
+    ovs = orc.render(scene, views)
+    gs, gw, counts, ga = orc.backward_scene(scene, ovs, [grads[v] for v in views], views, mode=terms,
+                                            want_attr=want_attr)
+    stats = []
+    for k, v in enumerate(views):
+        stats.append(parity.compare_view(gpu, v, ovs[k], gs[k], scene.tris))
+    if check_world and len(views) == scene.n_views:
+        ex = np.unique(np.concatenate([parity.excluded_vertices(scene.tris, gpu.index[v], ovs[k].index)
+                                       for k, v in enumerate(views)]))
+        nbad, worst = parity.grad_violations(gpu.grad_verts, gw, ex)
+        assert nbad == 0, f"world gradients: {nbad} components outside tolerance (worst {worst:.3g})"
+    if want_attr:
+        nbad, worst = parity.grad_violations(gpu.grad_attr, ga)
+        assert nbad == 0, f"attribute gradients: {nbad} outside tolerance (worst {worst:.3g})"
+    return gpu, stats, counts
+
+
+# ---------------------------------------------------------------------------
+# projection: snapped positions bit-exact
+# ---------------------------------------------------------------------------
+
+def test_project_snap_bitexact(orc):
+    import torch
+
+    from paper_2405_02508_gb300 import binding as B
+
+    sc = scenes.head_multiview(n_views=8, H=2048, W=1334, n=64)
+    verts = torch.from_numpy(sc.verts).cuda()
+    cams = B.cameras_tensor(sc.cams)
+    vpix = torch.empty((8, len(sc.verts), 8), dtype=torch.float32, device="cuda")
+    B.mer_project(verts, cams, vpix)
+    rec = vpix.cpu().numpy()
+    ints = rec.view(np.int32)
+    for v in range(8):
+        scr, snap, flags = orc.project(sc.verts, sc.cams[v])
+        np.testing.assert_array_equal(ints[v, :, 6], flags)
+        np.testing.assert_array_equal(ints[v, :, 0], snap[:, 0])
+        np.testing.assert_array_equal(ints[v, :, 1], snap[:, 1])
+        x = snap[:, 0] / 256.0 + rec[v, :, 2]
+        np.testing.assert_allclose(x, scr[:, 0], rtol=0, atol=1e-6)
+        z = rec[v, :, 4].astype(np.float64) + rec[v, :, 5]
+        np.testing.assert_allclose(z, scr[:, 2], rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# the five workloads
+# ---------------------------------------------------------------------------
+
+def test_parity_tiny_icosphere_l2(orc):
+    """128^2, 1280 triangles, L2 loss against a target from the perturbed copy."""
+    sc = scenes.tiny_icosphere()
+    tgt = Scene(sc.name, sc.target_verts, sc.tris, sc.cams, sc.H, sc.W, sc.attr, sc.shading)
+    It = orc.render(tgt)[0].image
+    Io = orc.render(sc)[0].image
+    g = (2.0 * (Io - It))[None].astype(np.float32)
+    gpu, stats, counts = run_parity(orc, sc, g, want_attr=True)
+    assert stats[0]["covered"] > 5000
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_parity_intersection_two_spheres(orc, tile):
+    """512^2, 2 x 20480 triangles interpenetrating: silhouettes and intersection micro-edges."""
+    sc = scenes.two_spheres()
+    gpu, stats, counts = run_parity(orc, sc, sc.upstream(), tile=tile)
+    assert counts[0]["intersection"] > 500
+
+
+def test_parity_intersections_off(orc):
+    sc = scenes.two_spheres(H=256, W=256)
+    run_parity(orc, sc, sc.upstream(), terms=1 | 2)
+
+
+def test_parity_edge_only_and_interior_only(orc):
+    sc = scenes.two_spheres(H=256, W=256, subdiv=4)
+    run_parity(orc, sc, sc.upstream(), terms=1 | 4)
+    run_parity(orc, sc, sc.upstream(), terms=2)
+
+
+@pytest.mark.parametrize("store_bary", [True, False])
+def test_parity_head_single_view(orc, store_bary):
+    """1024^2, 131k triangles, bilinear texture through interpolated UVs, RGB + mask."""
+    sc = scenes.head_single_view()
+    run_parity(orc, sc, sc.upstream(), want_attr=True, store_bary=store_bary)
+
+
+def test_parity_multiview_full_size_sampled_views(orc):
+    """32 views at 1334x2048 as the benchmark runs them; the oracle checks 3 sampled views."""
+    sc = scenes.head_multiview()
+    g = sc.upstream()
+    run_parity(orc, sc, g, views=[0, 13, 31], check_world=False)
+
+
+def test_parity_uneven_items(orc):
+    """Items of the uneven batch: smallest, largest and two in between."""
+    items = scenes.uneven_batch(n_items=256)
+    T = np.array([len(it.tris) for it in items])
+    order = np.argsort(T)
+    for i in [order[0], order[len(order) // 3], order[2 * len(order) // 3], order[-1]]:
+        it = items[i]
+        run_parity(orc, it, it.upstream())
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def _screen_scene(scr, tris, H, W, C=1, colours=None):
+    scr = np.asarray(scr, np.float64)
+    colours = np.linspace(0.1, 0.9, len(scr)).astype(np.float32)[:, None] if colours is None else colours
+    return scr, np.asarray(tris, np.int32).reshape(-1, 3), H, W, Shading(n_main=1, C=1, bg=[0.25]), colours
+
+
+def gpu_screen_run(scr, tris, H, W, sh, attr, grads, tile=16, terms=ALL):
+    import torch
+
+    from paper_2405_02508_gb300.render import Renderer
+
+    r = Renderer(torch.from_numpy(tris), len(scr), 1, H, W, sh, attr.shape[1], tile=tile)
+    r.project_screen(torch.from_numpy(scr[None]).cuda())
+    r.rasterize()
+    a = torch.from_numpy(attr).cuda()
+    r.shade(a, None)
+    r.grad_vpix.zero_()
+    from paper_2405_02508_gb300 import binding as B
+
+    B.mer_backward(r.vpix, r.tris, r.index, r.image, torch.from_numpy(grads).cuda(), a, None, r.sh, terms,
+                   r.grad_vpix, None, r.workspace)
+    r.check_status()
+    return r.index[0].cpu().numpy(), r.image[0].cpu().numpy(), r.grad_vpix[0].cpu().numpy()
+
+
+def oracle_screen_run(orc, scr, tris, H, W, sh, attr, grads, terms=ALL):
+    s, snap, flags = orc.snap_screen(scr)
+    index, tie, _ = orc.rasterize(s, snap, flags, tris, H, W)
+    img = orc.shade(s, tris, index, attr, sh)
+    gs, _, _ = orc.backward(s, snap, flags, tris, index, img, grads, attr, sh, mode=terms)
+    return index, tie, img, gs
+
+
+CASES = {
+    "ragged_37x53": (_screen_scene([[3.3, 2.1, 0.5], [50.2, 9.7, 0.6], [20.1, 35.2, 0.4],
+                                    [10.5, 20.2, 0.7], [45.3, 30.1, 0.3], [30.2, 1.2, 0.5]],
+                                   [[0, 1, 2], [3, 4, 5]], 37, 53)),
+    "one_pixel": _screen_scene([[-1.0, -1.0, 0.5], [3.0, -1.0, 0.5], [-1.0, 3.0, 0.5]], [[0, 1, 2]], 1, 1),
+    "row_1x40": _screen_scene([[2.2, -3.0, 0.5], [30.7, 0.5, 0.5], [11.1, 4.0, 0.5]], [[0, 1, 2]], 1, 40),
+    "column_40x1": _screen_scene([[-3.0, 2.2, 0.5], [0.5, 30.7, 0.5], [4.0, 11.1, 0.5]], [[0, 1, 2]], 40, 1),
+    "full_screen": _screen_scene([[-100, -100, 0.5], [400, -100, 0.5], [-100, 400, 0.5]], [[0, 1, 2]], 64, 64),
+    "all_background": _screen_scene([[-30, -30, 0.5], [-20, -30, 0.5], [-30, -20, 0.5]], [[0, 1, 2]], 32, 32),
+    "guard_band": _screen_scene([[-3.0e6, 5.0, 0.5], [40.0, 20.0, 0.5], [10.0, 60.0, 0.5],
+                                 [-1.0e5, -1.0e5, 0.5], [2.0e5, 10.0, 0.6], [15.0, 3.0e5, 0.4]],
+                                [[0, 1, 2], [3, 4, 5]], 64, 64),
+    "behind_camera": _screen_scene([[5.0, 5.0, -0.5], [40.0, 8.0, 0.5], [10.0, 50.0, 0.5],
+                                    [6.0, 6.0, 0.5], [50.0, 10.0, 0.5], [12.0, 55.0, 0.5]],
+                                   [[0, 1, 2], [3, 4, 5]], 64, 64),
+    "degenerate": _screen_scene([[5.0, 5.0, 0.5], [10.0, 10.0, 0.5], [20.0, 20.0, 0.5],
+                                 [4.0, 30.0, 0.5], [4.0, 30.0, 0.5], [40.0, 2.0, 0.5]],
+                                [[0, 1, 2], [3, 4, 5]], 48, 48),
+    "centres_on_edges": _screen_scene([[0.5, 0.5, 0.5], [20.5, 0.5, 0.5], [0.5, 20.5, 0.5], [20.5, 20.5, 0.5],
+                                       [10.5, 10.5, 0.6]],
+                                      [[0, 1, 4], [1, 3, 4], [3, 2, 4], [2, 0, 4]], 24, 24),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_edge_cases(orc, case, tile):
+    scr, tris, H, W, sh, attr = CASES[case]
+    g = np.random.default_rng(1).standard_normal((1, H, W, 1)).astype(np.float32)
+    gi, gimg, gg = gpu_screen_run(scr, tris, H, W, sh, attr, g, tile=tile)
+    oi, tie, oimg, og = oracle_screen_run(orc, scr, tris, H, W, sh, attr, g[0])
+    assert np.all((gi == oi) | tie)
+    np.testing.assert_allclose(gimg, oimg, rtol=parity.IMG_TOL, atol=parity.IMG_TOL)
+    nbad, worst = parity.grad_violations(gg, og)
+    assert nbad == 0, worst
+
+
+def test_empty_mesh_and_zero_sizes():
+    import torch
+
+    from paper_2405_02508_gb300 import binding as B
+    from paper_2405_02508_gb300.render import Renderer
+
+    sh = Shading(n_main=1, C=1, bg=[0.5])
+    r = Renderer(torch.zeros((0, 3), dtype=torch.int32), 0, 2, 20, 30, sh, 1)
+    r.project(torch.zeros((0, 3), device="cuda"), B.cameras_tensor(scenes.cameras_on_sphere(2, 3.0, 20, 30, 1)))
+    r.rasterize()
+    assert torch.all(r.index == -1)
+    r.shade(torch.zeros((0, 1), device="cuda"), None)
+    assert torch.all(r.image == 0.5)
+    r.grad_vpix.zero_()
+    B.mer_backward(r.vpix, r.tris, r.index, r.image, torch.ones_like(r.image), torch.zeros((0, 1), device="cuda"),
+                   None, r.sh, ALL, r.grad_vpix, None, r.workspace)
+    r.check_status()
+
+
+def test_bin_overflow_reported_and_recovered(orc):
+    """A workspace with room for 16 bin entries overflows; the status says so and the exact retry matches."""
+    import torch
+
+    from paper_2405_02508_gb300 import binding as B
+    from paper_2405_02508_gb300.render import Renderer
+
+    sc = scenes.tiny_icosphere()
+    r = Renderer(torch.from_numpy(sc.tris), len(sc.verts), 1, sc.H, sc.W, sc.shading, 3)
+    nbytes = B.mer_workspace_size(r.V, r.T, 1, sc.H, sc.W, 16, 16)
+    r.workspace = torch.zeros(nbytes // 4 + 64, dtype=torch.float32, device="cuda")
+    r.project(torch.from_numpy(sc.verts).cuda(), B.cameras_tensor(sc.cams))
+    B.mer_rasterize(r.vpix, r.tris, sc.H, sc.W, 16, r.workspace, r.index)
+    code, total = B.mer_sync_status(r.workspace)
+    assert code == B.MER_EOVERFLOW and total > 16
+    r.rasterize()  # checked path: resizes and redoes
+    ov = orc.render(sc)[0]
+    assert np.all((r.index[0].cpu().numpy() == ov.index) | ov.tie)
+
+
+def test_range_errors_reported():
+    import torch
+
+    from paper_2405_02508_gb300 import binding as B
+    from paper_2405_02508_gb300.render import Renderer
+
+    sh = Shading(n_main=1, C=1, bg=[0.5])
+    tris = torch.tensor([[0, 1, 7]], dtype=torch.int32)
+    r = Renderer(tris, 3, 1, 16, 16, sh, 1)
+    r.project_screen(torch.tensor([[[1.0, 1.0, 0.5], [10.0, 1.0, 0.5], [1.0, 10.0, 0.5]]], dtype=torch.float64).cuda())
+    with pytest.raises(B.MerError) as e:
+        r.rasterize()
+    assert e.value.code == B.MER_ERANGE
+
+
+def test_invalid_arguments_rejected():
+    import torch
+
+    from paper_2405_02508_gb300 import binding as B
+
+    lib = B.lib()
+    assert lib.mer_rasterize(None, 3, None, 1, 1, 16, 16, 16, None, 0, None, None, None, None) == B.MER_EINVAL
+    assert lib.mer_workspace_size(3, 1, 1, 16, 16, 12, 0) == 0  # tile must be 8, 16 or 32
+    ws = torch.zeros(1024, device="cuda")
+    assert lib.mer_rasterize(None, 3, None, 1, 1, 9000, 16, 16, B._ptr(ws), 4096, None, None, None, None) == B.MER_EINVAL
+
+
+def test_recompute_bary_bitwise_identical():
+    """Storing the barycentric image or not changes nothing downstream (the backward re-derives them)."""
+    sc = scenes.two_spheres(H=256, W=256, subdiv=4)
+    g = sc.upstream()
+    a = parity.gpu_run(sc, g, store_bary=True)
+    b = parity.gpu_run(sc, g, store_bary=False)
+    np.testing.assert_array_equal(a.index, b.index)
+    np.testing.assert_array_equal(a.image, b.image)
+    np.testing.assert_allclose(a.grad_verts, b.grad_verts, rtol=1e-5, atol=1e-6)  # atomics: order may differ
+
+
+def test_modular_entry_points_sum_to_fused(orc):
+    """mer_edge_grad_backward + mer_interpolate_backward reproduce the fused backward (plain interpolation)."""
+    import torch
+
+    from paper_2405_02508_gb300 import binding as B
+    from paper_2405_02508_gb300.render import Renderer
+
+    sc = scenes.tiny_icosphere()
+    g = sc.upstream()
+    fused = parity.gpu_run(sc, g)
+    r = Renderer(torch.from_numpy(sc.tris), len(sc.verts), 1, sc.H, sc.W, sc.shading, 3)
+    cams = B.cameras_tensor(sc.cams)
+    attr = torch.from_numpy(sc.attr).cuda()
+    r.forward(torch.from_numpy(sc.verts).cuda(), cams, attr)
+    gt = torch.from_numpy(g).cuda()
+    gv = torch.zeros_like(r.grad_vpix)
+    B.mer_edge_grad_backward(r.image, gt, r.index, r.vpix, r.tris, True, gv, r.workspace)
+    ga = torch.zeros_like(attr)
+    B.mer_interpolate_backward(attr, r.tris, r.vpix, r.index, gt, ga, gv, r.workspace)
+    r.check_status()
+    np.testing.assert_allclose(gv.cpu().numpy(), fused.grad_vpix, rtol=1e-4, atol=1e-6)
+
+
+def test_autograd_function_matches_renderer():
+    import torch
+
+    from paper_2405_02508_gb300 import binding as B
+    from paper_2405_02508_gb300.render import MerRender, Renderer
+
+    sc = scenes.head_single_view(H=256, W=256, n=32, tex_size=128)
+    g = torch.from_numpy(sc.upstream()).cuda()
+    ref = parity.gpu_run(sc, sc.upstream(), want_attr=True)
+    for recompute in (True, False):
+        r = Renderer(torch.from_numpy(sc.tris), len(sc.verts), 1, sc.H, sc.W, sc.shading, 2, sc.tex.shape)
+        verts = torch.from_numpy(sc.verts).cuda().requires_grad_(True)
+        attr = torch.from_numpy(sc.attr).cuda().requires_grad_(True)
+        img = MerRender.apply(verts, attr, torch.from_numpy(sc.tex).cuda(), B.cameras_tensor(sc.cams), r, recompute)
+        (img * g).sum().backward()
+        np.testing.assert_allclose(verts.grad.cpu().numpy(), ref.grad_verts, rtol=1e-4, atol=1e-5)
+        np.testing.assert_allclose(attr.grad.cpu().numpy(), ref.grad_attr, rtol=1e-4, atol=1e-5)
