@@ -149,29 +149,31 @@ int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, 
  *     with the screen barycentrics of the fragment's pixel centre.
  *   MER_INTERIOR: derivative of each covered pixel's shaded value with the
  *     index image fixed (Eq. 5 second term).
- * grad_vpix [n,V,3] float32 (+=): dL/d(x_s, y_s, zeta) per view.
+ * grad_vpix [n,V,3] float64 (+=): dL/d(x_s, y_s, zeta) per view.  The per-pixel
+ * arithmetic is FP32; the sums over pixels are accumulated in FP64 because a
+ * vertex gradient component can be a strongly cancelling sum of many terms.
  * grad_attr [V,C_attr] (+=) or NULL: dL/d(attr) of the interior term. */
 int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
                  const int32_t* index, const float* image, const float* grad_image,
                  const float* attr, const float* tex, const mer_shading* shading_host, int terms,
-                 float* grad_vpix, float* grad_attr, void* status_ws, void* stream);
+                 double* grad_vpix, float* grad_attr, void* status_ws, void* stream);
 
 /* EdgeGrad module backward alone (Supp. B): mer_backward with terms =
  * MER_EDGE | (intersections ? MER_INTERSECT : 0) for an image of C channels. */
 int mer_edge_grad_backward(const float* image, const float* grad_image, int C, const int32_t* index,
                            const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
-                           int intersections, float* grad_vpix, void* status_ws, void* stream);
+                           int intersections, double* grad_vpix, void* status_ws, void* stream);
 
 /* Interpolation module backward alone (Supp. B): interior term of plain
  * attribute interpolation, grad_out [n,H,W,C_attr] -> grad_attr [V,C_attr] (+=,
- * or NULL) and grad_vpix [n,V,3] (+=). */
+ * or NULL) and grad_vpix [n,V,3] float64 (+=). */
 int mer_interpolate_backward(const float* attr, int C_attr, const int32_t* tris, int T, const mer_vertex* vpix,
                              int V, const int32_t* index, int n, int H, int W, const float* grad_out,
-                             float* grad_attr, float* grad_vpix, void* status_ws, void* stream);
+                             float* grad_attr, double* grad_vpix, void* status_ws, void* stream);
 
 /* Vertex transform backward (Supp. B): grad_verts [V,3] (+=) = sum over views
  * of R^T J^T grad_vpix with J = d(x_s, y_s, zeta)/d(X_c, Y_c, Z_c). */
-int mer_project_backward(int V, const mer_camera* cams, int n, const mer_vertex* vpix, const float* grad_vpix,
+int mer_project_backward(int V, const mer_camera* cams, int n, const mer_vertex* vpix, const double* grad_vpix,
                          float* grad_verts, void* stream);
 
 /* Synchronises `stream`, reads and clears the device status word of a

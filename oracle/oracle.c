@@ -407,13 +407,16 @@ static void tri_normal(const double* scr, const int32_t* tri, double N[3])
  * r = sum_i lambda_i v_i, so dL/dv_i = lambda_i dL/dr (the interpolator's
  * backward, Sec. 4.2 last paragraph). */
 static void gather(const double* scr, const int32_t* tris, int t, int x, int y, const double g[3],
-                   double* grad_scr)
+                   double* grad_scr, double* grad_abs)
 {
     const int32_t* tri = tris + 3 * (size_t)t;
     double lam[3];
     screen_lambda(scr, tri, x + 0.5, y + 0.5, lam);
     for (int i = 0; i < 3; ++i)
-        for (int q = 0; q < 3; ++q) grad_scr[3 * (size_t)tri[i] + q] += lam[i] * g[q];
+        for (int q = 0; q < 3; ++q) {
+            grad_scr[3 * (size_t)tri[i] + q] += lam[i] * g[q];
+            if (grad_abs) grad_abs[3 * (size_t)tri[i] + q] += fabs(lam[i] * g[q]);
+        }
 }
 
 int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, int V,
@@ -421,7 +424,8 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                  const double* image /* [H,W,C] */, const float* grad_image /* [H,W,C] */,
                  const float* attr, const float* tex, const orc_shading* sh, int mode,
                  double* grad_scr /* [V,3], accumulated */, double* grad_attr /* [V,C_attr] or NULL */,
-                 int64_t* counts /* [6] */)
+                 int64_t* counts /* [6] */, double* grad_abs /* [V,3] or NULL */,
+                 double* grad_attr_abs /* [V,C_attr] or NULL */)
 {
     const int C = sh->C;
     dual I[64];
@@ -444,6 +448,7 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                         double acc = 0.0;
                         for (int c = 0; c < C; ++c) acc += (double)g[c] * I[c].d[3 * m + q];
                         grad_scr[3 * (size_t)tri[m] + q] += acc;
+                        if (grad_abs) grad_abs[3 * (size_t)tri[m] + q] += fabs(acc);
                     }
                 if (grad_attr) {
                     double lam[3], b[3], s = 0.0;
@@ -452,8 +457,10 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                     for (int i = 0; i < 3; ++i) b[i] = lam[i] * scr[3 * tri[i] + 2] / s;
                     if (sh->uv_offset < 0) {
                         for (int i = 0; i < 3; ++i)
-                            for (int c = 0; c < sh->n_main; ++c)
+                            for (int c = 0; c < sh->n_main; ++c) {
                                 grad_attr[(size_t)tri[i] * sh->C_attr + c] += b[i] * g[c];
+                                if (grad_attr_abs) grad_attr_abs[(size_t)tri[i] * sh->C_attr + c] += fabs(b[i] * g[c]);
+                            }
                     } else {
                         /* d(texture)/d(u, v) at the interpolated uv, via 2 tangents */
                         dual u = dvar(0.0, 0), v = dvar(0.0, 1);
@@ -469,6 +476,10 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                         for (int i = 0; i < 3; ++i) {
                             grad_attr[(size_t)tri[i] * sh->C_attr + sh->uv_offset] += b[i] * gu;
                             grad_attr[(size_t)tri[i] * sh->C_attr + sh->uv_offset + 1] += b[i] * gv;
+                            if (grad_attr_abs) {
+                                grad_attr_abs[(size_t)tri[i] * sh->C_attr + sh->uv_offset] += fabs(b[i] * gu);
+                                grad_attr_abs[(size_t)tri[i] * sh->C_attr + sh->uv_offset + 1] += fabs(b[i] * gv);
+                            }
                         }
                     }
                 }
@@ -523,8 +534,8 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                         ga[2] = dLdp * dpdr_a * nA[1];
                         gb[axis] = dLdp * dpdr_b * nB[0];
                         gb[2] = dLdp * dpdr_b * nB[1];
-                        gather(scr, tris, ta, xa, ya, ga, grad_scr);
-                        gather(scr, tris, tb, xb, yb, gb, grad_scr);
+                        gather(scr, tris, ta, xa, ya, ga, grad_scr, grad_abs);
+                        gather(scr, tris, tb, xb, yb, gb, grad_scr, grad_abs);
                         continue;
                     }
                     /* Overhang: the primitive on top is the one whose pixel centre
@@ -537,8 +548,55 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                  * 0 for the covered one (Sec. 4.3). */
                 double g[3] = {0, 0, 0};
                 g[axis] = dLdp;
-                if (fg == 0) gather(scr, tris, ta, xa, ya, g, grad_scr);
-                else gather(scr, tris, tb, xb, yb, g, grad_scr);
+                if (fg == 0) gather(scr, tris, ta, xa, ya, g, grad_scr, grad_abs);
+                else gather(scr, tris, tb, xb, yb, g, grad_scr, grad_abs);
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Texel-cell ambiguity (test helper, not part of the method).  The bilinear
+ * sampler's derivative jumps where the texel coordinate x = u*TW - 1/2 crosses
+ * an integer (or y reaches a clamp edge).  A pixel is flagged when x or y lies
+ * within eps of such a point, eps being a bound of the FP32 rounding error of
+ * the texel coordinate when it is formed as u_0 + sum_i b_i (u_i - u_0):
+ * eps_u = 32 ulp * sum_i |b_i||u_i - u_0| + 4 ulp * |u|, eps_x = TW eps_u + 2 ulp |x|
+ * (ulp = 2^-24).  Either one-sided derivative is correct at such pixels.
+ * ------------------------------------------------------------------------ */
+static int near_boundary(double x, double eps) { double f = x - floor(x); return f <= eps || 1.0 - f <= eps; }
+
+int orc_texel_ambiguity(const double* scr, const int32_t* tris, const int32_t* index, int H, int W,
+                        const float* attr, const orc_shading* sh, uint8_t* flags /* [H,W] */)
+{
+    const double ulp = 1.0 / 16777216.0;
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            flags[p] = 0;
+            int t = index[p];
+            if (t < 0 || sh->uv_offset < 0) continue;
+            const int32_t* tri = tris + 3 * (size_t)t;
+            double lam[3], b[3], s = 0.0;
+            screen_lambda(scr, tri, x + 0.5, y + 0.5, lam);
+            for (int i = 0; i < 3; ++i) s += lam[i] * scr[3 * tri[i] + 2];
+            for (int i = 0; i < 3; ++i) b[i] = lam[i] * scr[3 * tri[i] + 2] / s;
+            for (int axis = 0; axis < 2; ++axis) {
+                double a0 = attr[(size_t)tri[0] * sh->C_attr + sh->uv_offset + axis];
+                double u = 0.0, ext = 0.0;
+                for (int i = 0; i < 3; ++i) {
+                    double ai = attr[(size_t)tri[i] * sh->C_attr + sh->uv_offset + axis];
+                    u += b[i] * ai;
+                    ext += fabs(b[i]) * fabs(ai - a0);
+                }
+                int n = axis == 0 ? sh->tex_w : sh->tex_h;
+                double xc = u * n - 0.5;
+                double eps = n * (32.0 * ulp * ext + 4.0 * ulp * fabs(u)) + 2.0 * ulp * fabs(xc) + 1e-12;
+                int amb = 0;
+                if (axis == 0) amb = near_boundary(xc, eps);
+                else amb = fabs(xc) <= eps || fabs(xc - (n - 1)) <= eps || (xc > 0 && xc < n - 1 && near_boundary(xc, eps));
+                if (amb) flags[p] = 1;
             }
         }
     }

@@ -79,7 +79,9 @@ def lib():
         L.orc_pixel_values.restype = i
         L.orc_shade.argtypes = [P, P, P, i, i, P, P, P, ctypes.POINTER(OrcShading), P]
         L.orc_shade.restype = i
-        L.orc_backward.argtypes = [P, P, P, i, P, P, i, i, P, P, P, P, ctypes.POINTER(OrcShading), i, P, P, P]
+        L.orc_backward.argtypes = [P, P, P, i, P, P, i, i, P, P, P, P, ctypes.POINTER(OrcShading), i, P, P, P, P, P]
+        L.orc_texel_ambiguity.argtypes = [P, P, P, i, i, P, ctypes.POINTER(OrcShading), P]
+        L.orc_texel_ambiguity.restype = i
         L.orc_backward.restype = i
         L.orc_project_backward.argtypes = [P, i, ctypes.POINTER(OrcCamera), P, P]
         L.orc_project_backward.restype = None
@@ -180,8 +182,9 @@ def shade(scr, tris, index, attr, sh, tex=None):
 
 
 def backward(scr, snap, flags, tris, index, image, grad_image, attr, sh, tex=None,
-             mode: int = EDGE | INTERIOR | INTERSECT, want_attr: bool = False):
-    """-> grad_scr [V,3] f64, grad_attr [V,C_attr] or None, counts dict."""
+             mode: int = EDGE | INTERIOR | INTERSECT, want_attr: bool = False, want_abs: bool = False):
+    """-> grad_scr [V,3] f64, grad_attr [V,C_attr] or None, counts dict (+ grad_abs [V,3] if want_abs:
+    the sum of the absolute values of every per-pixel contribution, the conditioning of each sum)."""
     H, W = index.shape
     V = len(scr)
     attr = np.ascontiguousarray(attr, dtype=np.float32)
@@ -192,12 +195,33 @@ def backward(scr, snap, flags, tris, index, image, grad_image, attr, sh, tex=Non
     gs = np.zeros((V, 3))
     ga = np.zeros((V, attr.shape[1])) if want_attr else None
     counts = np.zeros(6, np.int64)
+    gabs = np.zeros((V, 3)) if want_abs else None
+    gaabs = np.zeros((V, attr.shape[1])) if (want_abs and want_attr) else None
     rc = lib().orc_backward(_p(scr), _p(snap), _p(flags), V, _p(np.ascontiguousarray(tris, dtype=np.int32)),
                             _p(np.ascontiguousarray(index, dtype=np.int32)), H, W, _p(image), _p(grad_image),
-                            _p(attr), _p(tex), ctypes.byref(s), mode, _p(gs), _p(ga), _p(counts))
+                            _p(attr), _p(tex), ctypes.byref(s), mode, _p(gs), _p(ga), _p(counts), _p(gabs),
+                            _p(gaabs))
     assert rc == 0
     names = ["differing", "overhang", "adjacent", "intersection", "intersection_parallel", "intersection_off"]
+    if want_abs:
+        cnt = dict(zip(names, counts.tolist()))
+        cnt["grad_attr_abs"] = gaabs
+        return gs, ga, cnt, gabs
     return gs, ga, dict(zip(names, counts.tolist()))
+
+
+def texel_ambiguity(scr, tris, index, attr, sh, tex):
+    """Pixels whose texel coordinate is within the FP32 error bound of a cell boundary ([H,W] bool)."""
+    H, W = index.shape
+    out = np.zeros((H, W), np.uint8)
+    if sh.uv_offset < 0 or tex is None:
+        return out.astype(bool)
+    attr = np.ascontiguousarray(attr, dtype=np.float32)
+    s = shading(sh, attr.shape[1], tex)
+    lib().orc_texel_ambiguity(_p(scr), _p(np.ascontiguousarray(tris, dtype=np.int32)),
+                              _p(np.ascontiguousarray(index, dtype=np.int32)), H, W, _p(attr), ctypes.byref(s),
+                              _p(out))
+    return out.astype(bool)
 
 
 def project_backward(verts, cam, grad_scr):
@@ -214,7 +238,7 @@ def project_backward(verts, cam, grad_scr):
 # ---------------------------------------------------------------------------
 
 class ViewResult:
-    __slots__ = ("scr", "snap", "flags", "index", "tie", "lam", "bary", "depth", "image")
+    __slots__ = ("scr", "snap", "flags", "index", "tie", "lam", "bary", "depth", "image", "texamb")
 
 
 def render_view(verts, tris, cam, H, W, attr, sh, tex=None) -> ViewResult:
@@ -223,6 +247,7 @@ def render_view(verts, tris, cam, H, W, attr, sh, tex=None) -> ViewResult:
     r.index, r.tie, _ = rasterize(r.scr, r.snap, r.flags, tris, H, W)
     r.lam, r.bary, r.depth = pixel_values(r.scr, tris, r.index)
     r.image = shade(r.scr, tris, r.index, attr, sh, tex)
+    r.texamb = texel_ambiguity(r.scr, tris, r.index, attr, sh, tex)
     return r
 
 
@@ -245,9 +270,10 @@ def backward_scene(scene, results: list[ViewResult], grad_images, views=None,
     def one(k):
         i = views[k]
         r = results[k]
-        gs, ga, cnt = backward(r.scr, r.snap, r.flags, scene.tris, r.index, r.image, grad_images[k],
-                               scene.attr, scene.shading, scene.tex, mode, want_attr)
+        gs, ga, cnt, gabs = backward(r.scr, r.snap, r.flags, scene.tris, r.index, r.image, grad_images[k],
+                                     scene.attr, scene.shading, scene.tex, mode, want_attr, want_abs=True)
         gw = project_backward(scene.verts, scene.cams[i], gs)
+        cnt["grad_abs"] = gabs
         return gs, ga, gw, cnt
 
     with _pool(threads) as ex:
@@ -259,3 +285,23 @@ def backward_scene(scene, results: list[ViewResult], grad_images, views=None,
     if want_attr:
         grad_attr = sum(o[1] for o in outs)
     return [o[0] for o in outs], grad_verts, [o[3] for o in outs], grad_attr
+
+
+def world_condition(scene, views, results, S_views):
+    """Conditioning sums of the world-space gradients: the per-view sums of |contribution| pushed
+    through |R^T J^T| (J = d(x_s, y_s, zeta)/d(X_c, Y_c, Z_c) at the oracle's projection)."""
+    Sw = np.zeros((len(scene.verts), 3))
+    for k, v in enumerate(views):
+        cam = scene.cams[v]
+        R = np.asarray(cam["R"], np.float64).reshape(3, 3)
+        scr = results[k].scr
+        z = scr[:, 2]
+        J = np.zeros((len(z), 3, 3))
+        J[:, 0, 0] = float(cam["fx"]) * z
+        J[:, 0, 2] = -(scr[:, 0] - float(cam["cx"])) * z
+        J[:, 1, 1] = float(cam["fy"]) * z
+        J[:, 1, 2] = -(scr[:, 1] - float(cam["cy"])) * z
+        J[:, 2, 2] = -z * z
+        M = np.abs(np.einsum("ji,vkj->vik", R, J))
+        Sw += np.einsum("vik,vk->vi", M, S_views[k])
+    return Sw

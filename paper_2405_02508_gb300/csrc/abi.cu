@@ -8,7 +8,7 @@
 
 extern "C" int mer_launch_project(const float*, int, const mer_camera*, int, mer_vertex*, cudaStream_t);
 extern "C" int mer_launch_project_screen(const double*, int, int, mer_vertex*, cudaStream_t);
-extern "C" int mer_launch_project_backward(int, const mer_camera*, int, const mer_vertex*, const float*, float*,
+extern "C" int mer_launch_project_backward(int, const mer_camera*, int, const mer_vertex*, const double*, float*,
                                            cudaStream_t);
 extern "C" size_t mer_raster_workspace_size(int, int, int, int, int, int, long long);
 extern "C" int mer_launch_rasterize(const mer_vertex*, int, const int*, int, int, int, int, int, void*, size_t, int*,
@@ -16,7 +16,7 @@ extern "C" int mer_launch_rasterize(const mer_vertex*, int, const int*, int, int
 extern "C" int mer_launch_shade(const mer_vertex*, int, const int*, int, int, int, int, const int*, const float*,
                                 const float*, const float*, const mer_shading*, float*, void*, cudaStream_t);
 extern "C" int mer_launch_backward(const mer_vertex*, int, const int*, int, int, int, int, const int*, const float*,
-                                   const float*, const float*, const float*, const mer_shading*, int, float*, float*,
+                                   const float*, const float*, const float*, const mer_shading*, int, double*, float*,
                                    void*, cudaStream_t);
 
 namespace {
@@ -110,7 +110,7 @@ int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, 
 
 int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W, const int32_t* index,
                  const float* image, const float* grad_image, const float* attr, const float* tex,
-                 const mer_shading* sh, int terms, float* grad_vpix, float* grad_attr, void* status_ws, void* stream) {
+                 const mer_shading* sh, int terms, double* grad_vpix, float* grad_attr, void* status_ws, void* stream) {
     if (V < 0 || T < 0 || !dims_ok(n, H, W) || !shading_ok(sh)) return MER_EINVAL;
     if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT)) return MER_EINVAL;
     if ((long long)n * H * W == 0 || terms == 0) return MER_OK;
@@ -126,7 +126,7 @@ int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int 
 
 int mer_edge_grad_backward(const float* image, const float* grad_image, int C, const int32_t* index,
                            const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
-                           int intersections, float* grad_vpix, void* status_ws, void* stream) {
+                           int intersections, double* grad_vpix, void* status_ws, void* stream) {
     mer_shading sh = {0, C, -1, -1, -1, 0, 0, 0};
     return mer_backward(vpix, V, tris, T, n, H, W, index, image, grad_image, nullptr, nullptr, &sh,
                         MER_EDGE | (intersections ? MER_INTERSECT : 0), grad_vpix, nullptr, status_ws, stream);
@@ -134,13 +134,13 @@ int mer_edge_grad_backward(const float* image, const float* grad_image, int C, c
 
 int mer_interpolate_backward(const float* attr, int C_attr, const int32_t* tris, int T, const mer_vertex* vpix, int V,
                              const int32_t* index, int n, int H, int W, const float* grad_out, float* grad_attr,
-                             float* grad_vpix, void* status_ws, void* stream) {
+                             double* grad_vpix, void* status_ws, void* stream) {
     mer_shading sh = {C_attr, C_attr, -1, -1, -1, C_attr, 0, 0};
     return mer_backward(vpix, V, tris, T, n, H, W, index, nullptr, grad_out, attr, nullptr, &sh, MER_INTERIOR,
                         grad_vpix, grad_attr, status_ws, stream);
 }
 
-int mer_project_backward(int V, const mer_camera* cams, int n, const mer_vertex* vpix, const float* grad_vpix,
+int mer_project_backward(int V, const mer_camera* cams, int n, const mer_vertex* vpix, const double* grad_vpix,
                          float* grad_verts, void* stream) {
     if (V < 0 || n < 0) return MER_EINVAL;
     if ((long long)V * n == 0) return MER_OK;

@@ -11,7 +11,8 @@
 //     pair (oriented left->right / top->bottom), then the Sec. 4.3 rule (p on
 //     top -> dp/dr = 1 on the pair axis) or Eq. 12 (intersection) for p's side.
 // The fragment gradient is gathered to the 3 vertices with p's screen
-// barycentrics (dL/dv_i = lambda_i dL/dr), with FP32 atomics into grad_vpix.
+// barycentrics (dL/dv_i = lambda_i dL/dr), with FP64 atomics into grad_vpix (the
+// per-pixel terms are FP32; the sums over pixels are kept in FP64).
 #include <cuda_runtime.h>
 
 #include "mer_device.cuh"
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kBT* kBT) k_backward(const mer_vertex* __restr
                                                       const int* __restrict__ index, const float* __restrict__ image,
                                                       const float* __restrict__ grad, const float* __restrict__ attr,
                                                       const float* __restrict__ tex, BwdArgs a,
-                                                      float* __restrict__ grad_vpix, float* __restrict__ grad_attr,
+                                                      double* __restrict__ grad_vpix, float* __restrict__ grad_attr,
                                                       void* ws) {
     __shared__ int sidx[kHalo][kHalo];
     const int tiles_per_view = a.ntx * a.nty;
@@ -114,31 +115,35 @@ __global__ void __launch_bounds__(kBT* kBT) k_backward(const mer_vertex* __restr
         const float z[3] = {rv[0]->zeta, rv[1]->zeta, rv[2]->zeta};
         const float s = B.lam[0] * z[0] + B.lam[1] * z[1] + B.lam[2] * z[2];
         const float is = 1.0f / s;
-        float b[3], G[3];
+        float b[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) b[k] = B.lam[k] * z[k] * is;
+        // G_k = dL/db_k.  Only the differences G_k - G_i enter (sum_i b_i = 1), so they are formed
+        // from attribute differences: D01 = G_0 - G_1, D02 = G_0 - G_2, D12 = G_1 - G_2.
+        float D01 = 0.f, D02 = 0.f, D12 = 0.f;
         const int Ca = a.sh.C_attr;
         if (a.sh.uv_offset < 0) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float acc = 0.f;
-                for (int c = 0; c < a.sh.n_main; ++c) acc += g[c] * __ldg(attr + (size_t)vid[k] * Ca + c);
-                G[k] = acc;
+            for (int c = 0; c < a.sh.n_main; ++c) {
+                const float a0 = __ldg(attr + (size_t)vid[0] * Ca + c);
+                const float a1 = __ldg(attr + (size_t)vid[1] * Ca + c);
+                const float a2 = __ldg(attr + (size_t)vid[2] * Ca + c);
+                D01 += g[c] * (a0 - a1);
+                D02 += g[c] * (a0 - a2);
+                D12 += g[c] * (a1 - a2);
             }
             if (grad_attr) {
                 for (int k = 0; k < 3; ++k)
                     for (int c = 0; c < a.sh.n_main; ++c) atomicAdd(grad_attr + (size_t)vid[k] * Ca + c, b[k] * g[c]);
             }
         } else {
-            float uvk[3][2];
-            float u = 0.f, w = 0.f;
+            float uk[3], vk[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                uvk[k][0] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset);
-                uvk[k][1] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1);
-                u += b[k] * uvk[k][0];
-                w += b[k] * uvk[k][1];
+                uk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset);
+                vk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1);
             }
+            const float u = uk[0] + (b[1] * (uk[1] - uk[0]) + b[2] * (uk[2] - uk[0]));
+            const float w = vk[0] + (b[1] * (vk[1] - vk[0]) + b[2] * (vk[2] - vk[0]));
             float val[kMaxC], du[kMaxC], dv[kMaxC];
             tex_sample(tex, a.sh.tex_h, a.sh.tex_w, a.sh.n_main, u, w, val, du, dv);
             float gu = 0.f, gv = 0.f;
@@ -146,8 +151,9 @@ __global__ void __launch_bounds__(kBT* kBT) k_backward(const mer_vertex* __restr
                 gu += g[c] * du[c];
                 gv += g[c] * dv[c];
             }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) G[k] = gu * uvk[k][0] + gv * uvk[k][1];
+            D01 = gu * (uk[0] - uk[1]) + gv * (vk[0] - vk[1]);
+            D02 = gu * (uk[0] - uk[2]) + gv * (vk[0] - vk[2]);
+            D12 = gu * (uk[1] - uk[2]) + gv * (vk[1] - vk[2]);
             if (grad_attr) {
                 for (int k = 0; k < 3; ++k) {
                     atomicAdd(grad_attr + (size_t)vid[k] * Ca + a.sh.uv_offset, b[k] * gu);
@@ -155,15 +161,16 @@ __global__ void __launch_bounds__(kBT* kBT) k_backward(const mer_vertex* __restr
                 }
             }
         }
+        // G_k - Gbar = sum_i b_i (G_k - G_i)
+        const float GmG[3] = {b[1] * D01 + b[2] * D02, b[2] * D12 - b[0] * D01, -(b[0] * D02 + b[1] * D12)};
         const float gZ = a.sh.depth_ch >= 0 ? g[a.sh.depth_ch] : 0.f;
-        const float Gb = b[0] * G[0] + b[1] * G[1] + b[2] * G[2];
         float wx = 0.f, wy = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float dl = z[k] * is * ((G[k] - Gb) - gZ * is);  // dL/d lambda_k
+            hz[k] = is * (GmG[k] - gZ * is);  // (dL/d zeta_k) / lambda_k
+            const float dl = z[k] * hz[k];     // dL/d lambda_k
             wx += dl * B.gx[k];
             wy += dl * B.gy[k];
-            hz[k] = is * ((G[k] - Gb) - gZ * is);                  // (dL/d zeta_k) / lambda_k
         }
         fx -= wx;
         fy -= wy;
@@ -229,14 +236,14 @@ __global__ void __launch_bounds__(kBT* kBT) k_backward(const mer_vertex* __restr
         }
     }
 
-    float* gv = grad_vpix + (size_t)view * a.V * 3;
+    double* gv = grad_vpix + (size_t)view * a.V * 3;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float l = B.lam[k];
         const float cx = l * fx, cy = l * fy, cz = l * (fz + hz[k]);
-        if (cx != 0.f) atomicAdd(gv + 3 * (size_t)vid[k], cx);
-        if (cy != 0.f) atomicAdd(gv + 3 * (size_t)vid[k] + 1, cy);
-        if (cz != 0.f) atomicAdd(gv + 3 * (size_t)vid[k] + 2, cz);
+        if (cx != 0.f) atomicAdd(gv + 3 * (size_t)vid[k], (double)cx);
+        if (cy != 0.f) atomicAdd(gv + 3 * (size_t)vid[k] + 1, (double)cy);
+        if (cz != 0.f) atomicAdd(gv + 3 * (size_t)vid[k] + 2, (double)cz);
     }
 }
 
@@ -246,7 +253,7 @@ using namespace mer;
 
 extern "C" int mer_launch_backward(const mer_vertex* vpix, int V, const int* tris, int T, int n, int H, int W,
                                    const int* index, const float* image, const float* grad_image, const float* attr,
-                                   const float* tex, const mer_shading* sh, int terms, float* grad_vpix,
+                                   const float* tex, const mer_shading* sh, int terms, double* grad_vpix,
                                    float* grad_attr, void* ws, cudaStream_t s) {
     BwdArgs a;
     a.sh = *sh;

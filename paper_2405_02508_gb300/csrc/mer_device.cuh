@@ -92,13 +92,6 @@ __device__ __forceinline__ float diff_of_products(float a, float d, float b, flo
     return f + e;
 }
 
-// Unsnapped position of a vertex relative to the pixel centre (px, py) in pixels.
-// The integer part is exact; the residual adds one rounding.
-__device__ __forceinline__ void rel_pos(const mer_vertex& v, int pxf, int pyf, float& dx, float& dy) {
-    dx = __fadd_rn(__int2float_rn(v.X - pxf) * (1.0f / 256.0f), v.rx);
-    dy = __fadd_rn(__int2float_rn(v.Y - pyf) * (1.0f / 256.0f), v.ry);
-}
-
 // Screen barycentrics of a pixel centre and their screen gradients.
 struct Bary {
     float lam[3];
@@ -106,28 +99,45 @@ struct Bary {
     float d;             // twice the signed area
 };
 
+// Barycentrics on the unsnapped geometry v = (X/256 + rx, Y/256 + ry).  With
+// a = (X - Px)/256, r = rx (and b, s for y) the edge function
+//   e_i = cross(v_j - P, v_k - P) = [a_j b_k - b_j a_k] + [a_j s_k + r_j b_k - b_j r_k - s_j a_k] + [r_j s_k - s_j r_k]
+// has an exact integer first bracket (the snapped edge function / 65536), so
+// e_i is accurate to about one ulp of itself even where it is small.
 __device__ __forceinline__ Bary screen_bary(const mer_vertex* v[3], int x, int y) {
     const int pxf = 256 * x + 128, pyf = 256 * y + 128;
-    float dx[3], dy[3];
+    int ix[3], iy[3];
+    float a[3], b[3], r[3], s[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) rel_pos(*v[i], pxf, pyf, dx[i], dy[i]);
-    Bary b;
+    for (int i = 0; i < 3; ++i) {
+        ix[i] = v[i]->X - pxf;
+        iy[i] = v[i]->Y - pyf;
+        a[i] = __int2float_rn(ix[i]) * (1.0f / 256.0f);
+        b[i] = __int2float_rn(iy[i]) * (1.0f / 256.0f);
+        r[i] = v[i]->rx;
+        s[i] = v[i]->ry;
+    }
+    Bary B;
     float e[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const int j = (i + 1) % 3, k = (i + 2) % 3;
-        e[i] = diff_of_products(dx[j], dy[k], dy[j], dx[k]);
+        const int64_t E = (int64_t)ix[j] * iy[k] - (int64_t)iy[j] * ix[k];
+        const float lin = (a[j] * s[k] - s[j] * a[k]) + (r[j] * b[k] - b[j] * r[k]);
+        const float quad = r[j] * s[k] - s[j] * r[k];
+        e[i] = __fmaf_rn(__ll2float_rn(E), 1.0f / 65536.0f, lin + quad);
     }
-    b.d = (e[0] + e[1]) + e[2];
-    const float inv = 1.0f / b.d;
+    B.d = (e[0] + e[1]) + e[2];
+    const float inv = 1.0f / B.d;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const int j = (i + 1) % 3, k = (i + 2) % 3;
-        b.lam[i] = e[i] * inv;
-        b.gx[i] = (dy[j] - dy[k]) * inv;
-        b.gy[i] = (dx[k] - dx[j]) * inv;
+        B.lam[i] = e[i] * inv;
+        // dy_j - dy_k and dx_k - dx_j from exact integer differences plus residuals
+        B.gx[i] = (__int2float_rn(iy[j] - iy[k]) * (1.0f / 256.0f) + (s[j] - s[k])) * inv;
+        B.gy[i] = (__int2float_rn(ix[k] - ix[j]) * (1.0f / 256.0f) + (r[k] - r[j])) * inv;
     }
-    return b;
+    return B;
 }
 
 // Bilinear texture sample (u wraps, v clamps), value and d/du, d/dv per channel.

@@ -61,30 +61,30 @@ __global__ void k_project_screen(const double* __restrict__ scr, int V, int n, m
 // One thread per vertex, looping over the views: grad_world = sum_views R^T J^T g,
 // J = d(x_s, y_s, zeta)/d(X_c, Y_c, Z_c) = [[fx z, 0, -(x_s-cx) z], [0, fy z, -(y_s-cy) z], [0, 0, -z^2]].
 __global__ void k_project_backward(int V, const mer_camera* __restrict__ cams, int n,
-                                   const mer_vertex* __restrict__ vpix, const float* __restrict__ grad_vpix,
+                                   const mer_vertex* __restrict__ vpix, const double* __restrict__ grad_vpix,
                                    float* __restrict__ grad_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;  // sum over views in FP64, products in FP32
     for (int view = 0; view < n; ++view) {
         const size_t k = (size_t)view * V + v;
         const mer_vertex r = vpix[k];
         if ((r.flags & 1u) == 0u) continue;
         const mer_camera& c = cams[view];
-        const float gx = grad_vpix[3 * k], gy = grad_vpix[3 * k + 1], gz = grad_vpix[3 * k + 2];
+        const float gx = (float)grad_vpix[3 * k], gy = (float)grad_vpix[3 * k + 1], gz = (float)grad_vpix[3 * k + 2];
         const float z = r.zeta;
         const float xs = (float)((double)r.X * (1.0 / 256.0) - c.cx) + r.rx;
         const float ys = (float)((double)r.Y * (1.0 / 256.0) - c.cy) + r.ry;
         const float gX = gx * (float)c.fx * z;
         const float gY = gy * (float)c.fy * z;
         const float gZ = -z * (gx * xs + gy * ys + gz * z);
-        a0 += (float)c.R[0] * gX + (float)c.R[3] * gY + (float)c.R[6] * gZ;
-        a1 += (float)c.R[1] * gX + (float)c.R[4] * gY + (float)c.R[7] * gZ;
-        a2 += (float)c.R[2] * gX + (float)c.R[5] * gY + (float)c.R[8] * gZ;
+        a0 += (double)((float)c.R[0] * gX + (float)c.R[3] * gY + (float)c.R[6] * gZ);
+        a1 += (double)((float)c.R[1] * gX + (float)c.R[4] * gY + (float)c.R[7] * gZ);
+        a2 += (double)((float)c.R[2] * gX + (float)c.R[5] * gY + (float)c.R[8] * gZ);
     }
-    grad_verts[3 * (size_t)v] += a0;
-    grad_verts[3 * (size_t)v + 1] += a1;
-    grad_verts[3 * (size_t)v + 2] += a2;
+    grad_verts[3 * (size_t)v] += (float)a0;
+    grad_verts[3 * (size_t)v + 1] += (float)a1;
+    grad_verts[3 * (size_t)v + 2] += (float)a2;
 }
 
 }  // namespace mer
@@ -107,7 +107,7 @@ extern "C" int mer_launch_project_screen(const double* scr, int V, int n, mer_ve
 }
 
 extern "C" int mer_launch_project_backward(int V, const mer_camera* cams, int n, const mer_vertex* vpix,
-                                           const float* grad_vpix, float* grad_verts, cudaStream_t s) {
+                                           const double* grad_vpix, float* grad_verts, cudaStream_t s) {
     if (V == 0 || n == 0) return 0;
     k_project_backward<<<(V + 255) / 256, 256, 0, s>>>(V, cams, n, vpix, grad_vpix, grad_verts);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;

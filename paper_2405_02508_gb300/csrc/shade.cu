@@ -54,12 +54,15 @@ __global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* _
                 out[c] = acc;
             }
         } else {
-            float u = 0.f, w = 0.f;
+            float uk[3], vk[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                u += b[k] * __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset);
-                w += b[k] * __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1);
+                uk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset);
+                vk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1);
             }
+            // relative to vertex 0: the error scales with the triangle's uv extent, not with |uv|
+            const float u = uk[0] + (b[1] * (uk[1] - uk[0]) + b[2] * (uk[2] - uk[0]));
+            const float w = vk[0] + (b[1] * (vk[1] - vk[0]) + b[2] * (vk[2] - vk[0]));
             tex_sample(tex, a.sh.tex_h, a.sh.tex_w, a.sh.n_main, u, w, out, nullptr, nullptr);
         }
         if (a.sh.mask_ch >= 0) out[a.sh.mask_ch] = 1.0f;

@@ -38,7 +38,7 @@ class Renderer:
         self.vpix = torch.empty((n, self.V, B.VERTEX_FLOATS), dtype=torch.float32, device=device)
         self.index = torch.empty((n, H, W), dtype=torch.int32, device=device)
         self.image = torch.empty((n, H, W, self.C), dtype=torch.float32, device=device)
-        self.grad_vpix = torch.zeros((n, self.V, 3), dtype=torch.float32, device=device)
+        self.grad_vpix = torch.zeros((n, self.V, 3), dtype=torch.float64, device=device)
         self.grad_verts = torch.zeros((self.V, 3), dtype=torch.float32, device=device)
         self._alloc_workspace(0)
 

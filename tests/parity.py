@@ -5,8 +5,16 @@ Tolerances (written here, used by every parity test):
 * index image: bit-exact on every pixel the oracle does not flag as a depth
   near-tie (relative zeta gap <= 1e-6); flagged pixels are counted.
 * image and depth values: |g - o| <= 1e-5 (1 + |o|).
-* vertex gradients (per view, and the world-space sum): |g - o| <= 1e-6 + 1e-4 |o|
-  per component, FP32 against FP64.
+* vertex gradients (per view, and the world-space sum), per component, FP32
+  arithmetic against FP64:  |g - o| <= 1e-6 + 1e-4 |o| + 2e-6 S, where S is the
+  sum of the absolute values of all per-pixel contributions to that component
+  (computed by the oracle).  A component is a sum of many signed terms; when
+  they cancel to far below S no FP32 evaluation of the terms can reach 1e-4 of
+  the result, so the bound also admits ~34 FP32 ulps of S.
+* pixels whose result is not unique are excluded with the vertices they touch:
+  depth near-ties whose index differs, and pixels whose texel coordinate lies
+  within the FP32 error bound of a texel-cell boundary (the bilinear derivative
+  is discontinuous there; either one-sided value is correct).
 """
 from __future__ import annotations
 
@@ -15,7 +23,7 @@ from dataclasses import dataclass
 import numpy as np
 
 IMG_TOL = 1e-5
-GRAD_ABS, GRAD_REL = 1e-6, 1e-4
+GRAD_ABS, GRAD_REL, GRAD_COND = 1e-6, 1e-4, 2e-6
 
 
 @dataclass
@@ -58,12 +66,16 @@ def gpu_run(scene, grad_images: np.ndarray, terms: int = 7, tile: int = 16, want
                      r.grad_verts.cpu().numpy(), None if ga is None else ga.cpu().numpy())
 
 
-def excluded_vertices(tris, idx_a, idx_b):
+def excluded_vertices(tris, idx_a, idx_b, ambiguous=None):
     """Vertices whose gradients may legitimately differ: triangles at pixels where the two index images
-    differ (flagged near-ties) and at their 4-neighbours."""
+    differ (flagged near-ties) and at their 4-neighbours, and triangles at texel-ambiguous pixels."""
     diff = idx_a != idx_b
+    extra = np.zeros(0, np.int64)
+    if ambiguous is not None and ambiguous.any():
+        ts = np.unique(idx_b[ambiguous & (idx_b >= 0)])
+        extra = np.unique(tris[ts].reshape(-1))
     if not diff.any():
-        return np.zeros(0, np.int64)
+        return extra
     m = diff.copy()
     m[1:, :] |= diff[:-1, :]
     m[:-1, :] |= diff[1:, :]
@@ -71,22 +83,23 @@ def excluded_vertices(tris, idx_a, idx_b):
     m[:, :-1] |= diff[:, 1:]
     ts = np.unique(np.concatenate([idx_a[m], idx_b[m]]))
     ts = ts[ts >= 0]
-    return np.unique(tris[ts].reshape(-1))
+    return np.unique(np.concatenate([tris[ts].reshape(-1), extra]))
 
 
-def grad_violations(g: np.ndarray, o: np.ndarray, exclude=None):
-    """Returns (number of violating components, worst |g-o| / (abs + rel |o|))."""
+def grad_violations(g: np.ndarray, o: np.ndarray, S=None, exclude=None):
+    """Returns (number of violating components, worst |g-o| / bound)."""
     g = np.asarray(g, np.float64)
     o = np.asarray(o, np.float64)
+    S = np.zeros_like(o) if S is None else np.asarray(S, np.float64)
     if exclude is not None and len(exclude):
         keep = np.ones(len(o), bool)
         keep[exclude] = False
-        g, o = g[keep], o[keep]
-    ratio = np.abs(g - o) / (GRAD_ABS + GRAD_REL * np.abs(o))
+        g, o, S = g[keep], o[keep], S[keep]
+    ratio = np.abs(g - o) / (GRAD_ABS + GRAD_REL * np.abs(o) + GRAD_COND * S)
     return int((ratio > 1.0).sum()), float(ratio.max() if ratio.size else 0.0)
 
 
-def compare_view(gpu: GpuResult, view: int, ov, orc_grad_scr, tris, check_grad=True):
+def compare_view(gpu: GpuResult, view: int, ov, orc_grad_scr, tris, check_grad=True, S=None):
     """Compare one view; returns a dict of statistics and asserts the parity bar."""
     gi = gpu.index[view]
     oi = ov.index
@@ -104,8 +117,14 @@ def compare_view(gpu: GpuResult, view: int, ov, orc_grad_scr, tris, check_grad=T
         assert db <= IMG_TOL, f"view {view}: bary error {db}"
     stats = {"ties": int(tie.sum()), "tie_mismatch": int((gi != oi).sum()), "covered": int((oi >= 0).sum())}
     if check_grad:
-        ex = excluded_vertices(tris, gi, oi)
-        nbad, worst = grad_violations(gpu.grad_vpix[view], orc_grad_scr, ex)
+        ex = excluded_vertices(tris, gi, oi, getattr(ov, "texamb", None))
+        nbad, worst = grad_violations(gpu.grad_vpix[view], orc_grad_scr, S, ex)
         stats.update(grad_bad=nbad, grad_worst=worst, excluded=len(ex))
         assert nbad == 0, f"view {view}: {nbad} gradient components outside tolerance (worst ratio {worst:.3g})"
     return stats
+
+
+def world_condition(scene, views, ovs, S_views):
+    import oracle
+
+    return oracle.world_condition(scene, views, ovs, S_views)
