@@ -273,21 +273,55 @@ int orc_pixel_values(const double* scr, const int32_t* tris, const int32_t* inde
  * (interior) term Omega of Eq. 5 / Eq. 11.
  * ------------------------------------------------------------------------ */
 #define ND 9
-typedef struct { double v; double d[ND]; } dual;
+/* v: value, d: derivatives.  m: magnitudes of the derivatives -- the same chain
+ * rule with every sum replaced by a sum of absolute values -- used only to report
+ * how strongly each derivative cancels (the conditioning the tests scale
+ * tolerances with); d never depends on m. */
+typedef struct { double v; double d[ND]; double m[ND]; } dual;
 
-static dual dconst(double v) { dual r; r.v = v; memset(r.d, 0, sizeof r.d); return r; }
-static dual dvar(double v, int k) { dual r = dconst(v); r.d[k] = 1.0; return r; }
-static dual dadd(dual a, dual b) { dual r; r.v = a.v + b.v; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] + b.d[k]; return r; }
-static dual dsub(dual a, dual b) { dual r; r.v = a.v - b.v; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] - b.d[k]; return r; }
-static dual dmul(dual a, dual b) { dual r; r.v = a.v * b.v; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k]; return r; }
+static dual dconst(double v) { dual r; r.v = v; memset(r.d, 0, sizeof r.d); memset(r.m, 0, sizeof r.m); return r; }
+static dual dvar(double v, int k) { dual r = dconst(v); r.d[k] = 1.0; r.m[k] = 1.0; return r; }
+static dual dadd(dual a, dual b)
+{
+    dual r;
+    r.v = a.v + b.v;
+    for (int k = 0; k < ND; ++k) { r.d[k] = a.d[k] + b.d[k]; r.m[k] = a.m[k] + b.m[k]; }
+    return r;
+}
+static dual dsub(dual a, dual b)
+{
+    dual r;
+    r.v = a.v - b.v;
+    for (int k = 0; k < ND; ++k) { r.d[k] = a.d[k] - b.d[k]; r.m[k] = a.m[k] + b.m[k]; }
+    return r;
+}
+static dual dmul(dual a, dual b)
+{
+    dual r;
+    r.v = a.v * b.v;
+    for (int k = 0; k < ND; ++k) {
+        r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+        r.m[k] = a.m[k] * fabs(b.v) + fabs(a.v) * b.m[k];
+    }
+    return r;
+}
 static dual ddiv(dual a, dual b)
 {
     dual r;
     r.v = a.v / b.v;
-    for (int k = 0; k < ND; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+    for (int k = 0; k < ND; ++k) {
+        r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+        r.m[k] = (a.m[k] + fabs(r.v) * b.m[k]) / fabs(b.v);
+    }
     return r;
 }
-static dual dscale(dual a, double c) { dual r; r.v = a.v * c; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * c; return r; }
+static dual dscale(dual a, double c)
+{
+    dual r;
+    r.v = a.v * c;
+    for (int k = 0; k < ND; ++k) { r.d[k] = a.d[k] * c; r.m[k] = a.m[k] * fabs(c); }
+    return r;
+}
 
 /* Bilinear texture lookup, texel centres at ((i + 1/2)/TW, (j + 1/2)/TH):
  * u wraps, v clamps to the edge texels.  Value and derivatives through (u, v). */
@@ -407,7 +441,7 @@ static void tri_normal(const double* scr, const int32_t* tri, double N[3])
  * r = sum_i lambda_i v_i, so dL/dv_i = lambda_i dL/dr (the interpolator's
  * backward, Sec. 4.2 last paragraph). */
 static void gather(const double* scr, const int32_t* tris, int t, int x, int y, const double g[3],
-                   double* grad_scr, double* grad_abs)
+                   double* grad_scr, const double gmag[3], double* grad_abs)
 {
     const int32_t* tri = tris + 3 * (size_t)t;
     double lam[3];
@@ -415,7 +449,7 @@ static void gather(const double* scr, const int32_t* tris, int t, int x, int y, 
     for (int i = 0; i < 3; ++i)
         for (int q = 0; q < 3; ++q) {
             grad_scr[3 * (size_t)tri[i] + q] += lam[i] * g[q];
-            if (grad_abs) grad_abs[3 * (size_t)tri[i] + q] += fabs(lam[i] * g[q]);
+            if (grad_abs) grad_abs[3 * (size_t)tri[i] + q] += fabs(lam[i]) * gmag[q];
         }
 }
 
@@ -445,10 +479,13 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                 const float* g = grad_image + p * C;
                 for (int m = 0; m < 3; ++m)
                     for (int q = 0; q < 3; ++q) {
-                        double acc = 0.0;
-                        for (int c = 0; c < C; ++c) acc += (double)g[c] * I[c].d[3 * m + q];
+                        double acc = 0.0, mag = 0.0;
+                        for (int c = 0; c < C; ++c) {
+                            acc += (double)g[c] * I[c].d[3 * m + q];
+                            mag += fabs((double)g[c]) * I[c].m[3 * m + q];
+                        }
                         grad_scr[3 * (size_t)tri[m] + q] += acc;
-                        if (grad_abs) grad_abs[3 * (size_t)tri[m] + q] += fabs(acc);
+                        if (grad_abs) grad_abs[3 * (size_t)tri[m] + q] += mag;
                     }
                 if (grad_attr) {
                     double lam[3], b[3], s = 0.0;
@@ -471,14 +508,19 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                         }
                         dual T[64];
                         tex_bilinear(tex, sh->tex_h, sh->tex_w, sh->n_main, u, v, T);
-                        double gu = 0.0, gv = 0.0;
-                        for (int c = 0; c < sh->n_main; ++c) { gu += g[c] * T[c].d[0]; gv += g[c] * T[c].d[1]; }
+                        double gu = 0.0, gv = 0.0, gum = 0.0, gvm = 0.0;
+                        for (int c = 0; c < sh->n_main; ++c) {
+                            gu += g[c] * T[c].d[0];
+                            gv += g[c] * T[c].d[1];
+                            gum += fabs((double)g[c]) * T[c].m[0];
+                            gvm += fabs((double)g[c]) * T[c].m[1];
+                        }
                         for (int i = 0; i < 3; ++i) {
                             grad_attr[(size_t)tri[i] * sh->C_attr + sh->uv_offset] += b[i] * gu;
                             grad_attr[(size_t)tri[i] * sh->C_attr + sh->uv_offset + 1] += b[i] * gv;
                             if (grad_attr_abs) {
-                                grad_attr_abs[(size_t)tri[i] * sh->C_attr + sh->uv_offset] += fabs(b[i] * gu);
-                                grad_attr_abs[(size_t)tri[i] * sh->C_attr + sh->uv_offset + 1] += fabs(b[i] * gv);
+                                grad_attr_abs[(size_t)tri[i] * sh->C_attr + sh->uv_offset] += fabs(b[i]) * gum;
+                                grad_attr_abs[(size_t)tri[i] * sh->C_attr + sh->uv_offset + 1] += fabs(b[i]) * gvm;
                             }
                         }
                     }
@@ -500,10 +542,13 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                 counts[0]++;
                 /* Eq. 11: dL/dp_AB = 1/2 (dL/dI_A + dL/dI_B)(I_A - I_B), summed over
                  * the channels of the image, with p increasing from A towards B. */
-                double dLdp = 0.0;
-                for (int c = 0; c < C; ++c)
-                    dLdp += 0.5 * ((double)grad_image[pa * C + c] + (double)grad_image[pb * C + c]) *
-                            (image[pa * C + c] - image[pb * C + c]);
+                double dLdp = 0.0, dLdp_mag = 0.0;
+                for (int c = 0; c < C; ++c) {
+                    double gm = 0.5 * ((double)grad_image[pa * C + c] + (double)grad_image[pb * C + c]);
+                    dLdp += gm * (image[pa * C + c] - image[pb * C + c]);
+                    /* conditioning w.r.t. the image values: |g| (|I_A| + |I_B|) */
+                    dLdp_mag += fabs(gm) * (fabs(image[pa * C + c]) + fabs(image[pb * C + c]));
+                }
                 /* Edge classification (Sec. 4.3, Supp. A.2). */
                 int fg = -1; /* 0: A's fragment overhangs, 1: B's */
                 if (ta < 0 || tb < 0) {
@@ -529,13 +574,17 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                         double dpdr_a = -nB[1] / den_a;
                         double den_b = nA[0] * nB[1] - nA[1] * nB[0]; /* v = B, f = A */
                         double dpdr_b = -nA[1] / den_b;
-                        double ga[3] = {0, 0, 0}, gb[3] = {0, 0, 0};
+                        double ga[3] = {0, 0, 0}, gb[3] = {0, 0, 0}, ma[3] = {0, 0, 0}, mb[3] = {0, 0, 0};
                         ga[axis] = dLdp * dpdr_a * nA[0];
                         ga[2] = dLdp * dpdr_a * nA[1];
                         gb[axis] = dLdp * dpdr_b * nB[0];
                         gb[2] = dLdp * dpdr_b * nB[1];
-                        gather(scr, tris, ta, xa, ya, ga, grad_scr, grad_abs);
-                        gather(scr, tris, tb, xb, yb, gb, grad_scr, grad_abs);
+                        ma[axis] = dLdp_mag * fabs(dpdr_a * nA[0]);
+                        ma[2] = dLdp_mag * fabs(dpdr_a * nA[1]);
+                        mb[axis] = dLdp_mag * fabs(dpdr_b * nB[0]);
+                        mb[2] = dLdp_mag * fabs(dpdr_b * nB[1]);
+                        gather(scr, tris, ta, xa, ya, ga, grad_scr, ma, grad_abs);
+                        gather(scr, tris, tb, xb, yb, gb, grad_scr, mb, grad_abs);
                         continue;
                     }
                     /* Overhang: the primitive on top is the one whose pixel centre
@@ -546,10 +595,11 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                 counts[1]++;
                 /* Overhang: dp/dr = 1 on the pair axis for the foreground fragment,
                  * 0 for the covered one (Sec. 4.3). */
-                double g[3] = {0, 0, 0};
+                double g[3] = {0, 0, 0}, m[3] = {0, 0, 0};
                 g[axis] = dLdp;
-                if (fg == 0) gather(scr, tris, ta, xa, ya, g, grad_scr, grad_abs);
-                else gather(scr, tris, tb, xb, yb, g, grad_scr, grad_abs);
+                m[axis] = dLdp_mag;
+                if (fg == 0) gather(scr, tris, ta, xa, ya, g, grad_scr, m, grad_abs);
+                else gather(scr, tris, tb, xb, yb, g, grad_scr, m, grad_abs);
             }
         }
     }
@@ -561,8 +611,8 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
  * sampler's derivative jumps where the texel coordinate x = u*TW - 1/2 crosses
  * an integer (or y reaches a clamp edge).  A pixel is flagged when x or y lies
  * within eps of such a point, eps being a bound of the FP32 rounding error of
- * the texel coordinate when it is formed as u_0 + sum_i b_i (u_i - u_0):
- * eps_u = 32 ulp * sum_i |b_i||u_i - u_0| + 4 ulp * |u|, eps_x = TW eps_u + 2 ulp |x|
+ * the texel coordinate when it is formed as the exact x_0 = u_0 TW - 1/2 plus the
+ * offset sum_i b_i (x_i - x_0):  eps = 32 ulp TW sum_i |b_i||u_i - u_0| + 4 ulp
  * (ulp = 2^-24).  Either one-sided derivative is correct at such pixels.
  * ------------------------------------------------------------------------ */
 static int near_boundary(double x, double eps) { double f = x - floor(x); return f <= eps || 1.0 - f <= eps; }
@@ -592,7 +642,7 @@ int orc_texel_ambiguity(const double* scr, const int32_t* tris, const int32_t* i
                 }
                 int n = axis == 0 ? sh->tex_w : sh->tex_h;
                 double xc = u * n - 0.5;
-                double eps = n * (32.0 * ulp * ext + 4.0 * ulp * fabs(u)) + 2.0 * ulp * fabs(xc) + 1e-12;
+                double eps = n * 32.0 * ulp * ext + 4.0 * ulp * fabs(xc - floor(xc)) + 1e-12;
                 int amb = 0;
                 if (axis == 0) amb = near_boundary(xc, eps);
                 else amb = fabs(xc) <= eps || fabs(xc - (n - 1)) <= eps || (xc > 0 && xc < n - 1 && near_boundary(xc, eps));

@@ -114,7 +114,7 @@ int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int 
     if (V < 0 || T < 0 || !dims_ok(n, H, W) || !shading_ok(sh)) return MER_EINVAL;
     if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT)) return MER_EINVAL;
     if ((long long)n * H * W == 0 || terms == 0) return MER_OK;
-    if (!index || !grad_image || !grad_vpix) return MER_EINVAL;
+    if (!index || !grad_image || (V > 0 && !grad_vpix)) return MER_EINVAL;
     if (T > 0 && (!tris || !vpix)) return MER_EINVAL;
     if ((terms & MER_EDGE) && !image) return MER_EINVAL;
     if ((terms & MER_INTERIOR) && sh->n_main > 0 && !attr) return MER_EINVAL;

@@ -142,10 +142,10 @@ __global__ void __launch_bounds__(kBT* kBT) k_backward(const mer_vertex* __restr
                 uk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset);
                 vk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1);
             }
-            const float u = uk[0] + (b[1] * (uk[1] - uk[0]) + b[2] * (uk[2] - uk[0]));
-            const float w = vk[0] + (b[1] * (vk[1] - vk[0]) + b[2] * (vk[2] - vk[0]));
+            const TexCoord cx = tex_coord(uk[0], uk[1], uk[2], b[1], b[2], a.sh.tex_w);
+            const TexCoord cy = tex_coord(vk[0], vk[1], vk[2], b[1], b[2], a.sh.tex_h);
             float val[kMaxC], du[kMaxC], dv[kMaxC];
-            tex_sample(tex, a.sh.tex_h, a.sh.tex_w, a.sh.n_main, u, w, val, du, dv);
+            tex_sample(tex, a.sh.tex_h, a.sh.tex_w, a.sh.n_main, cx, cy, val, du, dv);
             float gu = 0.f, gv = 0.f;
             for (int c = 0; c < a.sh.n_main; ++c) {
                 gu += g[c] * du[c];
@@ -164,14 +164,23 @@ __global__ void __launch_bounds__(kBT* kBT) k_backward(const mer_vertex* __restr
         // G_k - Gbar = sum_i b_i (G_k - G_i)
         const float GmG[3] = {b[1] * D01 + b[2] * D02, b[2] * D12 - b[0] * D01, -(b[0] * D02 + b[1] * D12)};
         const float gZ = a.sh.depth_ch >= 0 ? g[a.sh.depth_ch] : 0.f;
+        // w = sum_k (dL/d lambda_k) grad lambda_k with dL/d lambda_k = zeta_k is (GmG_k - gZ is).  The depth
+        // part -gZ is^2 sum_k zeta_k grad lambda_k equals -gZ is^2 sum_k (zeta_k - zeta_0) grad lambda_k
+        // (the gradients sum to zero); the zeta differences come from the hi + lo split, so the near
+        // cancellation of an almost constant zeta across the triangle costs no accuracy.
+        const float dz1 = (z[1] - z[0]) + (rv[1]->zeta_lo - rv[0]->zeta_lo);
+        const float dz2 = (z[2] - z[0]) + (rv[2]->zeta_lo - rv[0]->zeta_lo);
         float wx = 0.f, wy = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             hz[k] = is * (GmG[k] - gZ * is);  // (dL/d zeta_k) / lambda_k
-            const float dl = z[k] * hz[k];     // dL/d lambda_k
+            const float dl = z[k] * is * GmG[k];
             wx += dl * B.gx[k];
             wy += dl * B.gy[k];
         }
+        const float dep = gZ * is * is;
+        wx -= dep * (dz1 * B.gx[1] + dz2 * B.gx[2]);
+        wy -= dep * (dz1 * B.gy[1] + dz2 * B.gy[2]);
         fx -= wx;
         fy -= wy;
     }

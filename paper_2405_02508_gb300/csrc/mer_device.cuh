@@ -140,28 +140,58 @@ __device__ __forceinline__ Bary screen_bary(const mer_vertex* v[3], int x, int y
     return B;
 }
 
-// Bilinear texture sample (u wraps, v clamps), value and d/du, d/dv per channel.
-__device__ __forceinline__ void tex_sample(const float* __restrict__ tex, int TH, int TW, int nc, float u, float v,
-                                           float* val, float* du, float* dv) {
-    // non-finite or far-out coordinates sample at 0 (keeps every index exact and in range)
-    if (!(fabsf(u) < 1024.0f)) u = 0.0f;
-    if (!(fabsf(v) < 1024.0f)) v = 0.0f;
-    const float x = u * (float)TW - 0.5f;
-    const float x0f = floorf(x);
-    const float fx = x - x0f;
-    int i0 = (int)(x0f - floorf(x0f / (float)TW) * (float)TW);
+// Texel coordinate x = u*N - 1/2 of the interpolated u = u0 + b1 (u1 - u0) + b2 (u2 - u0), split into an
+// integer cell and a fraction in [0, 1).  The base x0 = u0*N - 1/2 is formed exactly (for N a power of two)
+// and only the small offset sum_i b_i (x_i - x0) carries rounding, so the fraction is accurate to far below
+// the FP32 resolution of u itself.  Non-finite or |u| >= 1024 samples at u = 0.
+struct TexCoord {
+    int cell;
+    float frac;
+};
+
+__device__ __forceinline__ TexCoord tex_coord(float u0, float u1, float u2, float b1, float b2, int N) {
+    const float u = u0 + (b1 * (u1 - u0) + b2 * (u2 - u0));
+    TexCoord t;
+    if (!(fabsf(u) < 1024.0f)) {
+        t.cell = -1;
+        t.frac = 0.5f;
+        return t;
+    }
+    const float Nf = (float)N;
+    const float xb = u0 * Nf - 0.5f;
+    const float d = b1 * ((u1 * Nf - 0.5f) - xb) + b2 * ((u2 * Nf - 0.5f) - xb);
+    const float fl = floorf(xb);
+    const float f = (xb - fl) + d;  // xb - fl is exact
+    const float c = floorf(f);
+    float fr = f - c;
+    int cell = (int)fl + (int)c;
+    if (fr >= 1.0f) {  // f just below an integer rounded up: the next cell at fraction 0
+        fr = 0.0f;
+        cell += 1;
+    }
+    t.cell = cell;
+    t.frac = fr;
+    return t;
+}
+
+// Bilinear texture sample at texel coordinates (cx, cy): u wraps, v clamps to the edge texels.
+// Value and derivatives d/du, d/dv per channel (du, dv may be null).
+__device__ __forceinline__ void tex_sample(const float* __restrict__ tex, int TH, int TW, int nc, TexCoord cx,
+                                           TexCoord cy, float* val, float* du, float* dv) {
+    int i0 = cx.cell % TW;
     if (i0 < 0) i0 += TW;
-    if (i0 >= TW) i0 -= TW;
-    i0 = min(max(i0, 0), TW - 1);
     const int i1 = (i0 + 1 == TW) ? 0 : i0 + 1;
-    float y = v * (float)TH - 0.5f;
+    const float fx = cx.frac;
+    int j0, j1;
+    float fy;
     bool clamped = false;
-    if (y < 0.0f) { y = 0.0f; clamped = true; }
-    if (y > (float)(TH - 1)) { y = (float)(TH - 1); clamped = true; }
-    const float y0f = floorf(y);
-    const float fy = y - y0f;
-    const int j0 = (int)y0f;
-    const int j1 = j0 + 1 < TH ? j0 + 1 : TH - 1;
+    if (cy.cell < 0) {
+        j0 = 0; j1 = TH > 1 ? 1 : 0; fy = 0.0f; clamped = true;
+    } else if (cy.cell > TH - 1 || (cy.cell == TH - 1 && cy.frac > 0.0f)) {
+        j0 = TH - 1; j1 = TH - 1; fy = 0.0f; clamped = true;
+    } else {
+        j0 = cy.cell; j1 = j0 + 1 < TH ? j0 + 1 : TH - 1; fy = cy.frac;
+    }
     const float* r0 = tex + (size_t)j0 * TW * nc;
     const float* r1 = tex + (size_t)j1 * TW * nc;
     for (int c = 0; c < nc; ++c) {

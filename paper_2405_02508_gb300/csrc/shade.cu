@@ -60,10 +60,9 @@ __global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* _
                 uk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset);
                 vk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1);
             }
-            // relative to vertex 0: the error scales with the triangle's uv extent, not with |uv|
-            const float u = uk[0] + (b[1] * (uk[1] - uk[0]) + b[2] * (uk[2] - uk[0]));
-            const float w = vk[0] + (b[1] * (vk[1] - vk[0]) + b[2] * (vk[2] - vk[0]));
-            tex_sample(tex, a.sh.tex_h, a.sh.tex_w, a.sh.n_main, u, w, out, nullptr, nullptr);
+            const TexCoord cx = tex_coord(uk[0], uk[1], uk[2], b[1], b[2], a.sh.tex_w);
+            const TexCoord cy = tex_coord(vk[0], vk[1], vk[2], b[1], b[2], a.sh.tex_h);
+            tex_sample(tex, a.sh.tex_h, a.sh.tex_w, a.sh.n_main, cx, cy, out, nullptr, nullptr);
         }
         if (a.sh.mask_ch >= 0) out[a.sh.mask_ch] = 1.0f;
         if (a.sh.depth_ch >= 0) out[a.sh.depth_ch] = is;

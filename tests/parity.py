@@ -7,10 +7,12 @@ Tolerances (written here, used by every parity test):
 * image and depth values: |g - o| <= 1e-5 (1 + |o|).
 * vertex gradients (per view, and the world-space sum), per component, FP32
   arithmetic against FP64:  |g - o| <= 1e-6 + 1e-4 |o| + 2e-6 S, where S is the
-  sum of the absolute values of all per-pixel contributions to that component
-  (computed by the oracle).  A component is a sum of many signed terms; when
-  they cancel to far below S no FP32 evaluation of the terms can reach 1e-4 of
-  the result, so the bound also admits ~34 FP32 ulps of S.
+  sum of the magnitudes of all per-pixel contributions to that component
+  (computed by the oracle; for the edge term of Eq. 11 the image difference
+  I_A - I_B enters as |I_A| + |I_B|, its conditioning when the image itself is
+  FP32).  A component is a sum of many signed terms; when they cancel to far
+  below S no FP32 evaluation of the terms can reach 1e-4 of the result, so the
+  bound also admits ~34 FP32 ulps of S.
 * pixels whose result is not unique are excluded with the vertices they touch:
   depth near-ties whose index differs, and pixels whose texel coordinate lies
   within the FP32 error bound of a texel-cell boundary (the bilinear derivative

@@ -12,13 +12,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
 
 MUTATIONS = {
-    "eq11_sign": ("(image[pa * C + c] - image[pb * C + c])", "(image[pb * C + c] - image[pa * C + c])"),
-    "eq11_half": ("dLdp += 0.5 * (", "dLdp += 1.0 * ("),
+    "eq11_sign": ("dLdp += gm * (image[pa * C + c] - image[pb * C + c]);",
+                  "dLdp += gm * (image[pb * C + c] - image[pa * C + c]);"),
+    "eq11_half": ("double gm = 0.5 * (", "double gm = 1.0 * ("),
     "overhang_foreground": ("fg = a_in_b ? 0 : 1;", "fg = a_in_b ? 1 : 0;"),
     "eq12_sign": ("double dpdr_a = -nB[1] / den_a;", "double dpdr_a = nB[1] / den_a;"),
     "eq12_slice_axis": ("double nA[2] = {NA[axis], NA[2]}", "double nA[2] = {NA[1 - axis], NA[2]}"),
-    "gather_pixel": ("else gather(scr, tris, tb, xb, yb, g, grad_scr, grad_abs);",
-                     "else gather(scr, tris, tb, xa, ya, g, grad_scr, grad_abs);"),
+    "gather_pixel": ("else gather(scr, tris, tb, xb, yb, g, grad_scr, m, grad_abs);",
+                     "else gather(scr, tris, tb, xa, ya, g, grad_scr, m, grad_abs);"),
     "perspective_bary": ("b[i] = ddiv(dmul(lam[i], z[i]), s);", "b[i] = lam[i];"),
     "depth_derivative": ("I[sh->depth_ch] = ddiv(dconst(1.0), s);", "I[sh->depth_ch] = dconst(1.0 / s.v);"),
     "dual_quotient_rule": ("(a.d[k] * b.v - a.v * b.d[k])", "(a.d[k] * b.v + a.v * b.d[k])"),
