@@ -339,5 +339,9 @@ def test_autograd_function_matches_renderer():
         attr = torch.from_numpy(sc.attr).cuda().requires_grad_(True)
         img = MerRender.apply(verts, attr, torch.from_numpy(sc.tex).cuda(), B.cameras_tensor(sc.cams), r, recompute)
         (img * g).sum().backward()
-        np.testing.assert_allclose(verts.grad.cpu().numpy(), ref.grad_verts, rtol=1e-4, atol=1e-5)
-        np.testing.assert_allclose(attr.grad.cpu().numpy(), ref.grad_attr, rtol=1e-4, atol=1e-5)
+        # same kernels as the reference run; only the order of the FP32 attribute atomics differs, so the
+        # bound is relative to the largest component (cancelling sums differ by summation-order noise)
+        np.testing.assert_allclose(verts.grad.cpu().numpy(), ref.grad_verts, rtol=1e-4,
+                                   atol=1e-6 * np.abs(ref.grad_verts).max())
+        np.testing.assert_allclose(attr.grad.cpu().numpy(), ref.grad_attr, rtol=1e-4,
+                                   atol=1e-5 * np.abs(ref.grad_attr).max())
