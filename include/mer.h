@@ -128,6 +128,28 @@ int mer_rasterize(const mer_vertex* vpix, int V, const int32_t* tris, int T, int
                   int tile, void* workspace, size_t workspace_bytes,
                   int32_t* index, float* depth, float* bary, void* stream);
 
+/* mer_rasterize without a workspace argument, for callers that cannot allocate device memory at the
+ * time they call -- code running while a stream is being captured into a CUDA graph (cudaMalloc is not
+ * allowed there), or a host framework or plugin that hands the library its buffers but exposes no
+ * device allocator.  The paper has no counterpart: this is a deployment variant of the rasterization
+ * module above, with the same arguments, results and status codes.
+ *
+ * The workspace is a 64 MiB array in the library's own device memory (a file-scope __device__ array:
+ * every GPU that loads the library holds it until the process exits).  The call rejects, with
+ * MER_EINVAL, sizes whose fixed workspace part does not fit in it: 256 B of header, 12 B per bin tile
+ * (n * ceil(H/tile) * ceil(W/tile) tiles), 48 B per (view, triangle); the rest holds the bin lists.
+ * When the bin lists do not fit, the results are not valid and *status (device int, or NULL) receives
+ * bit 0 (bit 1: a triangle index >= V).  *status is written on `stream` after the raster; read it once
+ * the stream has passed that point.
+ *
+ * The call allocates nothing.  Its first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call before any stream capture.
+ * All calls on a device share the one array and it keeps the last call's contents (each call clears the
+ * part that must start at zero): calls that overlap on the GPU -- on different streams, or from
+ * different host threads -- race and must be serialised by the caller. */
+int mer_rasterize_noalloc(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W, int tile,
+                          int32_t* index, float* depth, float* bary, int32_t* status, void* stream);
+
 /* Interpolation module + deferred shading (Supp. B): shaded image [n,H,W,C]
  * per `shading`; background pixels take bg[c] (host array of C floats, copied
  * into the kernel arguments).  attr [V, C_attr]; tex [tex_h, tex_w, n_main] or

@@ -49,6 +49,7 @@ _SIGS = {
     "mer_interpolate_backward": ([_P, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "mer_project_backward": ([_I, _P, _I, _P, _P, _P, _P], _I),
     "mer_sync_status": ([_P, ctypes.POINTER(ctypes.c_int64), _P], _I),
+    "mer_rasterize_noalloc": ([_P, _I, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P], _I),
 }
 
 _lib = None
@@ -191,3 +192,11 @@ def mer_sync_status(workspace) -> tuple[int, int]:
     tot = ctypes.c_int64(0)
     code = lib().mer_sync_status(_ptr(workspace), ctypes.byref(tot), _stream())
     return code, int(tot.value)
+
+
+def mer_rasterize_noalloc(vpix, tris, H, W, tile, index, depth=None, bary=None, status=None):
+    """mer_rasterize with the library's own fixed workspace (no device allocation by anyone at call time).
+    ``status``: optional device int32 tensor of one element receiving the status bits."""
+    n, V = vpix.shape[0], vpix.shape[1]
+    _check(lib().mer_rasterize_noalloc(_ptr(vpix), V, _ptr(tris), tris.shape[0], n, H, W, tile, _ptr(index),
+                                       _ptr(depth), _ptr(bary), _ptr(status), _stream()), "mer_rasterize_noalloc")

@@ -11,6 +11,8 @@
 //                   index / depth / bary
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "mer_device.cuh"
 
 namespace mer {
@@ -342,4 +344,62 @@ extern "C" int mer_launch_rasterize(const mer_vertex* vpix, int V, const int* tr
         default: return 1;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// mer_rasterize_noalloc: the same binning and raster with the workspace in a fixed device array owned by
+// the library, for callers that cannot allocate device memory when they call.
+// ---------------------------------------------------------------------------------------------------
+
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB on every GPU that loads the library
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace mer {
+__global__ void k_copy_status(const void* ws, int* status_out) {
+    *status_out = reinterpret_cast<const WsHeader*>(ws)->status;
+}
+}  // namespace mer
+
+extern "C" int mer_rasterize_noalloc(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
+                                     int tile, int32_t* index, float* depth, float* bary, int32_t* status,
+                                     void* stream) {
+    if (V < 0 || T < 0 || n < 0 || H < 0 || W < 0 || H > kMaxDim || W > kMaxDim) return MER_EINVAL;
+    if ((long long)n * H * W >= (1LL << 31)) return MER_EINVAL;
+    if (tile != 8 && tile != 16 && tile != 32) return MER_EINVAL;
+    if ((long long)n * H * W == 0) return MER_OK;
+    if (!index || (T > 0 && (!tris || !vpix))) return MER_EINVAL;
+    // the fixed part of the workspace (headers, per-tile counters, one record per view and triangle)
+    // must fit; what is left of the array holds the bin lists
+    if (raster_layout(V, T, n, H, W, tile, 1).total > kNoAllocScratchBytes) return MER_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MER_ECUDA;
+    void* ptr = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            // host code sees g_noalloc_scratch only as a stand-in symbol: look up its device address once
+            // per device, with that device current
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MER_ECUDA;
+            g_noalloc_ptr[dev] = p;
+        }
+        ptr = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // every call shares the array: clear the status word left by the previous call
+    if (cudaMemsetAsync(ptr, 0, sizeof(WsHeader), s) != cudaSuccess) return MER_ECUDA;
+    const int rc = mer_launch_rasterize(vpix, V, tris, T, n, H, W, tile, ptr, kNoAllocScratchBytes, index, depth,
+                                        bary, s);
+    if (rc != 0) return rc;
+    if (status) {
+        k_copy_status<<<1, 1, 0, s>>>(ptr, status);
+        if (cudaGetLastError() != cudaSuccess) return MER_ECUDA;
+    }
+    return MER_OK;
 }
