@@ -34,7 +34,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=32)
     ap.add_argument("--views", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()

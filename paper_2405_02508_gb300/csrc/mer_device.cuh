@@ -31,7 +31,7 @@ constexpr int kStatusRange = 2;
 // Per (view, triangle) raster record written by the binning pass, 48 bytes.
 struct TriRaster {
     int X[3], Y[3];   // snapped vertex positions
-    float zd[3];      // zeta_i / (E_0 + E_1 + E_2), FP32
+    float zd[3];      // zeta_i / |E_0 + E_1 + E_2|, FP32
     int flags;        // bits 0..2: edge i is top-left; bit 3: negative area; bit 31: culled
     short bx0, bx1, by0, by1;  // inclusive pixel bounding box of the covered centres
 };
@@ -75,12 +75,48 @@ __device__ __forceinline__ bool covers_pts(const int X[3], const int Y[3], int p
     return true;
 }
 
+// int64 -> float, round to nearest even, with integer instructions only (the hardware conversion of a
+// 64-bit integer runs on the FP64 pipe, which is narrow on GB300).  Normalise so the leading one is bit
+// 63, keep 24 bits, round on the next 8 bits plus a sticky bit for everything below.
+__device__ __forceinline__ float ll2f_rn(long long v) {
+    if (v == 0) return 0.0f;
+    unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)a);
+    a <<= lz;
+    const unsigned top = (unsigned)(a >> 32);
+    const bool sticky = (unsigned)a != 0u;
+    unsigned m = top >> 8;
+    const unsigned rem = top & 0xFFu;
+    if (rem > 0x80u || (rem == 0x80u && (sticky || (m & 1u)))) ++m;
+    unsigned e = 127u + 63u - (unsigned)lz;
+    if (m >> 24) {
+        m >>= 1;
+        ++e;
+    }
+    return __uint_as_float((e << 23) | (m & 0x7FFFFFu) | (v < 0 ? 0x80000000u : 0u));
+}
+
+// Non-negative int64 -> float, exact below 2^23 with one integer add and one float subtract (the bits of
+// 2^23 + v read as a float are exactly 2^23 + v); the general conversion otherwise.
+__device__ __forceinline__ float nonneg_ll2f_rn(long long v) {
+    if ((unsigned long long)v < (1ull << 23)) return __uint_as_float(0x4B000000u + (unsigned)v) - 8388608.0f;
+    return ll2f_rn(v);
+}
+
+__device__ __forceinline__ float signed_ll2f_rn(long long v) {
+    const float f = nonneg_ll2f_rn(v < 0 ? -v : v);
+    return v < 0 ? -f : f;
+}
+
 // FP32 depth key: sum_i E_i * (zeta_i / sum E) with correctly rounded conversions
 // and an FMA chain (relative error <= 7 * 2^-24, see the design notes).
+// zd_i = zeta_i / |sum E| and |E_i| (E_i has the sign of the area at a covered pixel), so every term is >= 0.
 __device__ __forceinline__ float depth_key(const TriRaster& t, const int64_t E[3]) {
-    float z = __fmul_rn(__ll2float_rn(E[0]), t.zd[0]);
-    z = __fmaf_rn(__ll2float_rn(E[1]), t.zd[1], z);
-    z = __fmaf_rn(__ll2float_rn(E[2]), t.zd[2], z);
+    const bool neg = (t.flags & 8) != 0;
+    const long long e0 = neg ? -E[0] : E[0], e1 = neg ? -E[1] : E[1], e2 = neg ? -E[2] : E[2];
+    float z = __fmul_rn(nonneg_ll2f_rn(e0), t.zd[0]);
+    z = __fmaf_rn(nonneg_ll2f_rn(e1), t.zd[1], z);
+    z = __fmaf_rn(nonneg_ll2f_rn(e2), t.zd[2], z);
     return z;
 }
 
@@ -125,7 +161,7 @@ __device__ __forceinline__ Bary screen_bary(const mer_vertex* v[3], int x, int y
         const int64_t E = (int64_t)ix[j] * iy[k] - (int64_t)iy[j] * ix[k];
         const float lin = (a[j] * s[k] - s[j] * a[k]) + (r[j] * b[k] - b[j] * r[k]);
         const float quad = r[j] * s[k] - s[j] * r[k];
-        e[i] = __fmaf_rn(__ll2float_rn(E), 1.0f / 65536.0f, lin + quad);
+        e[i] = __fmaf_rn(signed_ll2f_rn(E), 1.0f / 65536.0f, lin + quad);
     }
     B.d = (e[0] + e[1]) + e[2];
     const float inv = 1.0f / B.d;
@@ -174,37 +210,59 @@ __device__ __forceinline__ TexCoord tex_coord(float u0, float u1, float u2, floa
     return t;
 }
 
-// Bilinear texture sample at texel coordinates (cx, cy): u wraps, v clamps to the edge texels.
-// Value and derivatives d/du, d/dv per channel (du, dv may be null).
-__device__ __forceinline__ void tex_sample(const float* __restrict__ tex, int TH, int TW, int nc, TexCoord cx,
-                                           TexCoord cy, float* val, float* du, float* dv) {
-    int i0 = cx.cell % TW;
-    if (i0 < 0) i0 += TW;
-    const int i1 = (i0 + 1 == TW) ? 0 : i0 + 1;
-    const float fx = cx.frac;
-    int j0, j1;
-    float fy;
-    bool clamped = false;
+// The four taps and weights of a bilinear lookup at texel coordinates (cx, cy): u wraps, v clamps to the
+// edge texels (a clamped v has zero derivative).
+struct TexTaps {
+    int i0, i1, j0, j1;
+    float fx, fy;
+    bool clamped;
+};
+
+__device__ __forceinline__ TexTaps tex_taps(int TH, int TW, TexCoord cx, TexCoord cy) {
+    TexTaps t;
+    t.i0 = cx.cell % TW;
+    if (t.i0 < 0) t.i0 += TW;
+    t.i1 = (t.i0 + 1 == TW) ? 0 : t.i0 + 1;
+    t.fx = cx.frac;
+    t.clamped = false;
     if (cy.cell < 0) {
-        j0 = 0; j1 = TH > 1 ? 1 : 0; fy = 0.0f; clamped = true;
+        t.j0 = 0; t.j1 = TH > 1 ? 1 : 0; t.fy = 0.0f; t.clamped = true;
     } else if (cy.cell > TH - 1 || (cy.cell == TH - 1 && cy.frac > 0.0f)) {
-        j0 = TH - 1; j1 = TH - 1; fy = 0.0f; clamped = true;
+        t.j0 = TH - 1; t.j1 = TH - 1; t.fy = 0.0f; t.clamped = true;
     } else {
-        j0 = cy.cell; j1 = j0 + 1 < TH ? j0 + 1 : TH - 1; fy = cy.frac;
+        t.j0 = cy.cell; t.j1 = t.j0 + 1 < TH ? t.j0 + 1 : TH - 1; t.fy = cy.frac;
     }
-    const float* r0 = tex + (size_t)j0 * TW * nc;
-    const float* r1 = tex + (size_t)j1 * TW * nc;
+    return t;
+}
+
+// Bilinear value of channel c.
+__device__ __forceinline__ float tex_value(const float* __restrict__ tex, int TW, int nc, const TexTaps& t, int c) {
+    const float* r0 = tex + (size_t)t.j0 * TW * nc;
+    const float* r1 = tex + (size_t)t.j1 * TW * nc;
+    const float t00 = __ldg(r0 + (size_t)t.i0 * nc + c), t10 = __ldg(r0 + (size_t)t.i1 * nc + c);
+    const float t01 = __ldg(r1 + (size_t)t.i0 * nc + c), t11 = __ldg(r1 + (size_t)t.i1 * nc + c);
+    const float a = t00 + t.fx * (t10 - t00);
+    const float b = t01 + t.fx * (t11 - t01);
+    return a + t.fy * (b - a);
+}
+
+// sum_c g_c dT_c/du and sum_c g_c dT_c/dv (g read from global memory, nc channels).
+__device__ __forceinline__ void tex_grad_uv(const float* __restrict__ tex, int TH, int TW, int nc, const TexTaps& t,
+                                            const float* __restrict__ g, float& gu, float& gv) {
+    const float* r0 = tex + (size_t)t.j0 * TW * nc;
+    const float* r1 = tex + (size_t)t.j1 * TW * nc;
+    float su = 0.f, sv = 0.f;
     for (int c = 0; c < nc; ++c) {
-        const float t00 = __ldg(r0 + (size_t)i0 * nc + c), t10 = __ldg(r0 + (size_t)i1 * nc + c);
-        const float t01 = __ldg(r1 + (size_t)i0 * nc + c), t11 = __ldg(r1 + (size_t)i1 * nc + c);
-        const float a = t00 + fx * (t10 - t00);
-        const float b = t01 + fx * (t11 - t01);
-        val[c] = a + fy * (b - a);
-        if (du) {
-            du[c] = (float)TW * ((1.0f - fy) * (t10 - t00) + fy * (t11 - t01));
-            dv[c] = clamped ? 0.0f : (float)TH * (b - a);
-        }
+        const float t00 = __ldg(r0 + (size_t)t.i0 * nc + c), t10 = __ldg(r0 + (size_t)t.i1 * nc + c);
+        const float t01 = __ldg(r1 + (size_t)t.i0 * nc + c), t11 = __ldg(r1 + (size_t)t.i1 * nc + c);
+        const float gc = __ldg(g + c);
+        su += gc * ((1.0f - t.fy) * (t10 - t00) + t.fy * (t11 - t01));
+        const float a = t00 + t.fx * (t10 - t00);
+        const float b = t01 + t.fx * (t11 - t01);
+        sv += gc * (b - a);
     }
+    gu = (float)TW * su;
+    gv = t.clamped ? 0.0f : (float)TH * sv;
 }
 
 __device__ __forceinline__ void set_status(void* ws, int bit) {

@@ -81,7 +81,7 @@ __global__ void k_setup_count(const mer_vertex* __restrict__ vpix, const int* __
         if (ga > 0 || (ga == 0 && gb > 0)) fl |= 1 << e;
     }
     r.flags = fl;
-    const float Df = __ll2float_rn(a2);
+    const float Df = ll2f_rn(a2 < 0 ? -a2 : a2);
 #pragma unroll
     for (int k = 0; k < 3; ++k) r.zd[k] = __fdiv_rn(v[k].zeta, Df);
     r.bx0 = (short)x0; r.bx1 = (short)x1; r.by0 = (short)y0; r.by1 = (short)y1;
@@ -175,45 +175,37 @@ __global__ void k_bin_fill(const TriRaster* __restrict__ recs, BinGeom g, const 
 }
 
 // --- raster ---
+// One CTA per (view, tile).  The tile's triangle records are staged in shared memory; each warp takes one
+// triangle at a time and its lanes test the pixels of the triangle's bounding box inside the tile (32 at a
+// time), so the work follows the bounding-box areas and every lane of a warp runs the same triangle.  The
+// nearest fragment per pixel is resolved in a shared-memory z-buffer by a 64-bit atomicMax on
+// (depth key bits << 32 | ~triangle id): larger depth key wins, equal keys go to the lower id.
 constexpr int kStage = 256;  // triangle records staged per round
+constexpr int kRasterThreads = 256;
 
 template <int TS>
-struct RasterCfg {
-    static constexpr int threads = TS * TS < 256 ? TS * TS : 256;
-    static constexpr int ppt = TS * TS / threads;  // pixels per thread
-};
-
-template <int TS>
-__global__ void __launch_bounds__(RasterCfg<TS>::threads) k_raster(const TriRaster* __restrict__ recs, BinGeom g,
+__global__ void __launch_bounds__(kRasterThreads) k_raster(const TriRaster* __restrict__ recs, BinGeom g,
                                                            const int* __restrict__ offs, const int* __restrict__ cnts,
                                                            const int* __restrict__ list, const mer_vertex* __restrict__ vpix,
                                                            const int* __restrict__ tris, void* ws, long long capacity,
                                                            int* __restrict__ index, float* __restrict__ depth,
                                                            float* __restrict__ bary) {
-    constexpr int kRasterThreads = RasterCfg<TS>::threads;
-    constexpr int PPT = RasterCfg<TS>::ppt;
     __shared__ TriRaster sh[kStage];
     __shared__ int sh_id[kStage];
+    __shared__ unsigned long long zbuf[TS * TS];
     const WsHeader* hdr = reinterpret_cast<const WsHeader*>(ws);
     const bool overflow = hdr->total_bins > capacity;
     const long long tile = blockIdx.x;
     const int view = (int)(tile / g.tiles_per_view);
     const int local = (int)(tile % g.tiles_per_view);
     const int ty = local / g.ntx, tx = local % g.ntx;
-    int px[PPT], py[PPT];
-    float bz[PPT];
-    int bid[PPT];
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int p = threadIdx.x + k * kRasterThreads;
-        px[k] = tx * TS + (p % TS);
-        py[k] = ty * TS + (p / TS);
-        bz[k] = -1.0f;
-        bid[k] = -1;
-    }
+    const int ox = tx * TS, oy = ty * TS;
+    for (int i = threadIdx.x; i < TS * TS; i += kRasterThreads) zbuf[i] = 0ull;
     const int count = overflow ? 0 : cnts[tile];
     const int off = overflow ? 0 : offs[tile];
     const TriRaster* rv = recs + (size_t)view * g.T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarps = kRasterThreads / 32;
     for (int base = 0; base < count; base += kStage) {
         const int m = min(kStage, count - base);
         __syncthreads();
@@ -223,34 +215,41 @@ __global__ void __launch_bounds__(RasterCfg<TS>::threads) k_raster(const TriRast
             sh_id[j] = t;
         }
         __syncthreads();
-        for (int j = 0; j < m; ++j) {
+        for (int j = warp; j < m; j += kWarps) {
             const TriRaster& r = sh[j];
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (px[k] < r.bx0 || px[k] > r.bx1 || py[k] < r.by0 || py[k] > r.by1) continue;
+            const int x0 = max((int)r.bx0, ox), x1 = min((int)r.bx1, ox + TS - 1);
+            const int y0 = max((int)r.by0, oy), y1 = min((int)r.by1, oy + TS - 1);
+            const int bw = x1 - x0 + 1, bh = y1 - y0 + 1;
+            if (bw <= 0 || bh <= 0) continue;
+            const int npx = bw * bh;
+            const float inv_bw = 1.0f / (float)bw;
+            const unsigned idkey = 0xFFFFFFFFu - (unsigned)sh_id[j];
+            for (int i = lane; i < npx; i += 32) {
+                const int dy = (int)(((float)i + 0.5f) * inv_bw);  // exact: the fraction stays >= 1/(2 bw)
+                const int dx = i - dy * bw;
+                const int px = x0 + dx, py = y0 + dy;
                 int64_t E[3];
-                if (!covers(r, 256 * px[k] + 128, 256 * py[k] + 128, E)) continue;
+                if (!covers(r, 256 * px + 128, 256 * py + 128, E)) continue;
                 const float z = depth_key(r, E);
-                const int id = sh_id[j];
-                if (z > bz[k] || (z == bz[k] && id < bid[k])) {
-                    bz[k] = z;
-                    bid[k] = id;
-                }
+                const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | idkey;
+                atomicMax(&zbuf[(py - oy) * TS + (px - ox)], key);
             }
         }
     }
+    __syncthreads();
     const mer_vertex* vb = vpix + (size_t)view * g.V;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        if (px[k] >= g.W || py[k] >= g.H) continue;
-        const size_t p = ((size_t)view * g.H + py[k]) * g.W + px[k];
-        const int t = bid[k];
+    for (int i = threadIdx.x; i < TS * TS; i += kRasterThreads) {
+        const int px = ox + (i % TS), py = oy + (i / TS);
+        if (px >= g.W || py >= g.H) continue;
+        const unsigned long long key = zbuf[i];
+        const int t = key ? (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull)) : -1;
+        const size_t p = ((size_t)view * g.H + py) * g.W + px;
         index[p] = t;
         if (!depth && !bary) continue;
         float Z = 0.f, b1 = 0.f, b2 = 0.f;
         if (t >= 0) {
             const mer_vertex* v[3] = {vb + tris[3 * (size_t)t], vb + tris[3 * (size_t)t + 1], vb + tris[3 * (size_t)t + 2]};
-            const Bary B = screen_bary(v, px[k], py[k]);
+            const Bary B = screen_bary(v, px, py);
             const float z0 = v[0]->zeta, z1 = v[1]->zeta, z2 = v[2]->zeta;
             const float s = B.lam[0] * z0 + B.lam[1] * z1 + B.lam[2] * z2;
             const float is = 1.0f / s;
@@ -338,9 +337,9 @@ extern "C" int mer_launch_rasterize(const mer_vertex* vpix, int V, const int* tr
     }
     const unsigned grid = (unsigned)L.ntiles;
     switch (tile) {
-        case 8: k_raster<8><<<grid, RasterCfg<8>::threads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
-        case 16: k_raster<16><<<grid, RasterCfg<16>::threads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
-        case 32: k_raster<32><<<grid, RasterCfg<32>::threads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
+        case 8: k_raster<8><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
+        case 16: k_raster<16><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
+        case 32: k_raster<32><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
         default: return 1;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 2;

@@ -62,7 +62,8 @@ __global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* _
             }
             const TexCoord cx = tex_coord(uk[0], uk[1], uk[2], b[1], b[2], a.sh.tex_w);
             const TexCoord cy = tex_coord(vk[0], vk[1], vk[2], b[1], b[2], a.sh.tex_h);
-            tex_sample(tex, a.sh.tex_h, a.sh.tex_w, a.sh.n_main, cx, cy, out, nullptr, nullptr);
+            const TexTaps taps = tex_taps(a.sh.tex_h, a.sh.tex_w, cx, cy);
+            for (int c = 0; c < a.sh.n_main && c < kMaxC; ++c) out[c] = tex_value(tex, a.sh.tex_w, a.sh.n_main, taps, c);
         }
         if (a.sh.mask_ch >= 0) out[a.sh.mask_ch] = 1.0f;
         if (a.sh.depth_ch >= 0) out[a.sh.depth_ch] = is;

@@ -297,8 +297,8 @@ def test_recompute_bary_bitwise_identical():
     b = parity.gpu_run(sc, g, store_bary=False)
     np.testing.assert_array_equal(a.index, b.index)
     np.testing.assert_array_equal(a.image, b.image)
-    # FP64 atomics: the summation order may differ between runs, nothing else does
-    np.testing.assert_allclose(a.grad_verts, b.grad_verts, rtol=1e-6, atol=1e-9)
+    # the order of the per-tile FP32 partial sums and of the FP64 atomics may differ between runs, nothing else
+    np.testing.assert_allclose(a.grad_verts, b.grad_verts, rtol=1e-5, atol=1e-6 * np.abs(a.grad_verts).max())
 
 
 def test_modular_entry_points_sum_to_fused(orc):
