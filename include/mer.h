@@ -73,7 +73,9 @@ typedef struct mer_vertex {
 
 /* Layout of the shaded image [n,H,W,C] (deferred shading, Supp. B).
  * Channels [0, n_main) hold interpolated attribute channels 0..n_main-1
- * (uv_offset < 0), or the bilinear texture [tex_h, tex_w, n_main] sampled at the
+ * (uv_offset < 0), or the bilinear texture [tex_h, tex_w, tex_c] (channels 0..n_main-1 used; tex_c =
+ * floats per texel in memory, 0 meaning n_main; tex_c = 4 with a 16-byte aligned texture reads each texel
+ * with one 128-bit load) sampled at the
  * interpolated (u, v) = attribute channels (uv_offset, uv_offset+1) with u
  * wrapping and v clamped, texel centres at ((i+1/2)/tex_w, (j+1/2)/tex_h).
  * mask_ch / depth_ch (or -1) hold the coverage mask (1 on triangles) and the
@@ -86,6 +88,7 @@ typedef struct mer_shading {
     int depth_ch;
     int C_attr;  /* channels per vertex of `attr` */
     int tex_h, tex_w;
+    int tex_c;   /* floats per texel in memory (>= n_main), 0 = n_main */
 } mer_shading;
 
 /* Terms computed by mer_backward (bit mask). */
@@ -152,7 +155,7 @@ int mer_rasterize_noalloc(const mer_vertex* vpix, int V, const int32_t* tris, in
 
 /* Interpolation module + deferred shading (Supp. B): shaded image [n,H,W,C]
  * per `shading`; background pixels take bg[c] (host array of C floats, copied
- * into the kernel arguments).  attr [V, C_attr]; tex [tex_h, tex_w, n_main] or
+ * into the kernel arguments).  attr [V, C_attr]; tex [tex_h, tex_w, tex_c] or
  * NULL when uv_offset < 0. */
 int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
               const int32_t* index, const float* attr, const float* tex, const float* bg_host,

@@ -37,6 +37,7 @@ typedef struct {
     int depth_ch;  /* channel holding depth Z, or -1 */
     int C_attr;    /* attribute channels per vertex */
     int tex_h, tex_w;
+    int tex_c;     /* floats per texel in memory (>= n_main) */
 } orc_shading;
 
 enum { ORC_VALID_FRONT = 1, ORC_VALID_GUARD = 2, ORC_VALID = 3 };
@@ -325,7 +326,7 @@ static dual dscale(dual a, double c)
 
 /* Bilinear texture lookup, texel centres at ((i + 1/2)/TW, (j + 1/2)/TH):
  * u wraps, v clamps to the edge texels.  Value and derivatives through (u, v). */
-static void tex_bilinear(const float* tex, int TH, int TW, int nc, dual u, dual v, dual* out)
+static void tex_bilinear(const float* tex, int TH, int TW, int nc, int stride, dual u, dual v, dual* out)
 {
     /* non-finite or far-out coordinates (|u| or |v| >= 1024) sample at 0 */
     if (!(fabs(u.v) < 1024.0)) u = dconst(0.0);
@@ -347,8 +348,8 @@ static void tex_bilinear(const float* tex, int TH, int TW, int nc, dual u, dual 
     dual w00 = dmul(dsub(one, fx), dsub(one, fy)), w10 = dmul(fx, dsub(one, fy));
     dual w01 = dmul(dsub(one, fx), fy), w11 = dmul(fx, fy);
     for (int c = 0; c < nc; ++c) {
-        double t00 = tex[((size_t)j0 * TW + i0) * nc + c], t10 = tex[((size_t)j0 * TW + i1) * nc + c];
-        double t01 = tex[((size_t)j1 * TW + i0) * nc + c], t11 = tex[((size_t)j1 * TW + i1) * nc + c];
+        double t00 = tex[((size_t)j0 * TW + i0) * stride + c], t10 = tex[((size_t)j0 * TW + i1) * stride + c];
+        double t01 = tex[((size_t)j1 * TW + i0) * stride + c], t11 = tex[((size_t)j1 * TW + i1) * stride + c];
         out[c] = dadd(dadd(dscale(w00, t00), dscale(w10, t10)), dadd(dscale(w01, t01), dscale(w11, t11)));
     }
 }
@@ -383,7 +384,7 @@ static void shade_pixel_dual(const double* scr, const int32_t* tri, double px, d
             u = dadd(u, dscale(b[i], attr[(size_t)tri[i] * sh->C_attr + sh->uv_offset]));
             v = dadd(v, dscale(b[i], attr[(size_t)tri[i] * sh->C_attr + sh->uv_offset + 1]));
         }
-        tex_bilinear(tex, sh->tex_h, sh->tex_w, sh->n_main, u, v, I);
+        tex_bilinear(tex, sh->tex_h, sh->tex_w, sh->n_main, sh->tex_c, u, v, I);
     }
     if (sh->mask_ch >= 0) I[sh->mask_ch] = dconst(1.0);
     if (sh->depth_ch >= 0) I[sh->depth_ch] = ddiv(dconst(1.0), s);
@@ -507,7 +508,7 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                             v.v += b[i] * attr[(size_t)tri[i] * sh->C_attr + sh->uv_offset + 1];
                         }
                         dual T[64];
-                        tex_bilinear(tex, sh->tex_h, sh->tex_w, sh->n_main, u, v, T);
+                        tex_bilinear(tex, sh->tex_h, sh->tex_w, sh->n_main, sh->tex_c, u, v, T);
                         double gu = 0.0, gv = 0.0, gum = 0.0, gvm = 0.0;
                         for (int c = 0; c < sh->n_main; ++c) {
                             gu += g[c] * T[c].d[0];

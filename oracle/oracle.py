@@ -42,7 +42,7 @@ class OrcCamera(ctypes.Structure):
 class OrcShading(ctypes.Structure):
     _fields_ = [("n_main", ctypes.c_int), ("C", ctypes.c_int), ("uv_offset", ctypes.c_int),
                 ("mask_ch", ctypes.c_int), ("depth_ch", ctypes.c_int), ("C_attr", ctypes.c_int),
-                ("tex_h", ctypes.c_int), ("tex_w", ctypes.c_int)]
+                ("tex_h", ctypes.c_int), ("tex_w", ctypes.c_int), ("tex_c", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -109,6 +109,7 @@ def shading(sh, C_attr: int, tex: np.ndarray | None) -> OrcShading:
     s.n_main, s.C, s.uv_offset, s.mask_ch, s.depth_ch = sh.n_main, sh.C, sh.uv_offset, sh.mask_ch, sh.depth_ch
     s.C_attr = C_attr
     s.tex_h, s.tex_w = (tex.shape[0], tex.shape[1]) if tex is not None else (0, 0)
+    s.tex_c = tex.shape[2] if tex is not None else 0
     return s
 
 

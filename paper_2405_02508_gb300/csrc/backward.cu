@@ -17,6 +17,8 @@
 // tile's per-vertex totals go to grad_vpix with one FP64 atomic per component.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "mer_device.cuh"
 
 namespace mer {
@@ -31,6 +33,8 @@ struct BwdArgs {
     int terms;
     int n, H, W, V, T;
     int ntx, nty;
+    int tex_stride;  // floats per texel
+    bool tex_vec4;   // stride 4 and 16-byte aligned: 128-bit texel loads
 };
 
 // Vertex ids of triangle t; false if one is out of range.
@@ -44,13 +48,13 @@ __device__ __forceinline__ bool tri_ids(const int* __restrict__ tris, int t, int
 }
 
 // Plane normal (v1 - v0) x (v2 - v0) in (x_s, y_s, zeta) from accurate differences.
-__device__ __forceinline__ void tri_normal(const mer_vertex* const r[3], float N[3]) {
+__device__ __forceinline__ void tri_normal(const VRec r[3], float N[3]) {
     float e[2][3];
 #pragma unroll
     for (int k = 1; k < 3; ++k) {
-        e[k - 1][0] = __int2float_rn(r[k]->X - r[0]->X) * (1.0f / 256.0f) + (r[k]->rx - r[0]->rx);
-        e[k - 1][1] = __int2float_rn(r[k]->Y - r[0]->Y) * (1.0f / 256.0f) + (r[k]->ry - r[0]->ry);
-        e[k - 1][2] = (r[k]->zeta - r[0]->zeta) + (r[k]->zeta_lo - r[0]->zeta_lo);
+        e[k - 1][0] = i2f_exact(r[k].X - r[0].X) * (1.0f / 256.0f) + (r[k].rx - r[0].rx);
+        e[k - 1][1] = i2f_exact(r[k].Y - r[0].Y) * (1.0f / 256.0f) + (r[k].ry - r[0].ry);
+        e[k - 1][2] = (r[k].zeta - r[0].zeta) + (r[k].zeta_lo - r[0].zeta_lo);
     }
     N[0] = diff_of_products(e[0][1], e[1][2], e[0][2], e[1][1]);
     N[1] = diff_of_products(e[0][2], e[1][0], e[0][0], e[1][2]);
@@ -69,7 +73,7 @@ __device__ __forceinline__ int table_slot(int* keys, int vid) {
     return -1;
 }
 
-__global__ void __launch_bounds__(kThreads) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
+__global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
                                                        const int* __restrict__ index, const float* __restrict__ image,
                                                        const float* __restrict__ grad, const float* __restrict__ attr,
                                                        const float* __restrict__ tex, BwdArgs a,
@@ -114,13 +118,13 @@ __global__ void __launch_bounds__(kThreads) k_backward(const mer_vertex* __restr
     if (t >= 0) {
         const size_t p = (size_t)view * plane + (size_t)y * a.W + x;
         const float* gp = grad + p * C;
-        const mer_vertex* rv[3] = {vb + vid[0], vb + vid[1], vb + vid[2]};
+        const VRec rv[3] = {load_vrec(vb + vid[0]), load_vrec(vb + vid[1]), load_vrec(vb + vid[2])};
         const Bary B = screen_bary(rv, x, y);
         float fx = 0.f, fy = 0.f, fz = 0.f;
         float hz[3] = {0.f, 0.f, 0.f};
 
         if (a.terms & MER_INTERIOR) {
-            const float z[3] = {rv[0]->zeta, rv[1]->zeta, rv[2]->zeta};
+            const float z[3] = {rv[0].zeta, rv[1].zeta, rv[2].zeta};
             const float s = B.lam[0] * z[0] + B.lam[1] * z[1] + B.lam[2] * z[2];
             const float is = 1.0f / s;
             float b[3];
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_backward(const mer_vertex* __restr
                 const TexCoord cy = tex_coord(vk[0], vk[1], vk[2], b[1], b[2], a.sh.tex_h);
                 const TexTaps taps = tex_taps(a.sh.tex_h, a.sh.tex_w, cx, cy);
                 float gu, gv;
-                tex_grad_uv(tex, a.sh.tex_h, a.sh.tex_w, a.sh.n_main, taps, gp, gu, gv);
+                tex_grad_uv(tex, a.sh.tex_h, a.sh.tex_w, a.tex_stride, a.tex_vec4, a.sh.n_main, taps, gp, gu, gv);
                 D01 = gu * (uk[0] - uk[1]) + gv * (vk[0] - vk[1]);
                 D02 = gu * (uk[0] - uk[2]) + gv * (vk[0] - vk[2]);
                 D12 = gu * (uk[1] - uk[2]) + gv * (vk[1] - vk[2]);
@@ -175,8 +179,8 @@ __global__ void __launch_bounds__(kThreads) k_backward(const mer_vertex* __restr
             // part -gZ is^2 sum_k zeta_k grad lambda_k equals -gZ is^2 sum_k (zeta_k - zeta_0) grad lambda_k
             // (the gradients sum to zero); the zeta differences come from the hi + lo split, so the near
             // cancellation of an almost constant zeta across the triangle costs no accuracy.
-            const float dz1 = (z[1] - z[0]) + (rv[1]->zeta_lo - rv[0]->zeta_lo);
-            const float dz2 = (z[2] - z[0]) + (rv[2]->zeta_lo - rv[0]->zeta_lo);
+            const float dz1 = (z[1] - z[0]) + (rv[1].zeta_lo - rv[0].zeta_lo);
+            const float dz2 = (z[2] - z[0]) + (rv[2].zeta_lo - rv[0].zeta_lo);
             float wx = 0.f, wy = 0.f;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -196,8 +200,8 @@ __global__ void __launch_bounds__(kThreads) k_backward(const mer_vertex* __restr
             int X[3], Y[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                X[k] = rv[k]->X;
-                Y[k] = rv[k]->Y;
+                X[k] = rv[k].X;
+                Y[k] = rv[k].Y;
             }
             const float* ip = image + p * C;
 #pragma unroll 1
@@ -217,14 +221,15 @@ __global__ void __launch_bounds__(kThreads) k_backward(const mer_vertex* __restr
                     }
                     int Xq[3], Yq[3];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        Xq[k] = vb[vq[k]].X;
-                        Yq[k] = vb[vq[k]].Y;
+                    for (int k = 0; k < 3; ++k) {  // snapped position only: one 64-bit load per vertex
+                        const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
+                        Xq[k] = xy.x;
+                        Yq[k] = xy.y;
                     }
                     // classification (Sec. 4.3): p's fragment scatters only if p's centre lies inside q's
                     // triangle (p on top of it), or both centres lie in each other's triangles (intersection)
-                    if (!covers_pts(Xq, Yq, 256 * x + 128, 256 * y + 128)) continue;
-                    if (covers_pts(X, Y, 256 * qx + 128, 256 * qy + 128)) {
+                    if (!covers_xy(Xq, Yq, 256 * x + 128, 256 * y + 128)) continue;
+                    if (covers_xy(X, Y, 256 * qx + 128, 256 * qy + 128)) {
                         if (!(a.terms & MER_INTERSECT)) continue;
                         inter = true;
                     }
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_backward(const mer_vertex* __restr
                     continue;
                 }
                 // Eq. 12: p's triangle varies (v), q's triangle is fixed (f), slice (axis, zeta)
-                const mer_vertex* rq[3] = {vb + vq[0], vb + vq[1], vb + vq[2]};
+                const VRec rq[3] = {load_vrec(vb + vq[0]), load_vrec(vb + vq[1]), load_vrec(vb + vq[2])};
                 float Nv[3], Nf[3];
                 tri_normal(rv, Nv);
                 tri_normal(rq, Nf);
@@ -273,8 +278,18 @@ __global__ void __launch_bounds__(kThreads) k_backward(const mer_vertex* __restr
     const bool head = lane == 0 || tprev != t;
     const unsigned heads = __ballot_sync(full, head);
     const int seg = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of this run
+    const bool contributes = t >= 0 && (c0[0] != 0.f || c1[0] != 0.f || c2[0] != 0.f || c0[1] != 0.f ||
+                                        c1[1] != 0.f || c2[1] != 0.f || c0[2] != 0.f || c1[2] != 0.f ||
+                                        c2[2] != 0.f);
+    const unsigned any = __ballot_sync(full, contributes);
+    // longest run in the warp decides how many doubling steps the scan needs
+    const int runlen = t >= 0 ? lane - seg + 1 : 0;  // runs of background lanes carry nothing
+    int maxrun = runlen;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxrun = max(maxrun, __shfl_xor_sync(full, maxrun, o));
 #pragma unroll
     for (int dlt = 1; dlt < 32; dlt <<= 1) {
+        if (!any || dlt >= maxrun) break;
         const bool take = lane - dlt >= seg;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -291,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_backward(const mer_vertex* __restr
     const int tnext = __shfl_down_sync(full, t, 1);
     const bool tail = lane == 31 || tnext != t;
     double* gvv = grad_vpix + (size_t)view * a.V * 3;
-    if (tail && t >= 0) {
+    if (tail && t >= 0 && any) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int sl = table_slot(skey, vid[k]);
@@ -331,6 +346,8 @@ extern "C" int mer_launch_backward(const mer_vertex* vpix, int V, const int* tri
     a.n = n; a.H = H; a.W = W; a.V = V; a.T = T;
     a.ntx = (W + kTW - 1) / kTW;
     a.nty = (H + kTH - 1) / kTH;
+    a.tex_stride = sh->tex_c > 0 ? sh->tex_c : sh->n_main;
+    a.tex_vec4 = a.tex_stride == 4 && tex && (reinterpret_cast<uintptr_t>(tex) & 15u) == 0;
     const long long blocks = (long long)a.ntx * a.nty * n;
     if (blocks == 0) return 0;
     k_backward<<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, image, grad_image, attr, tex, a, grad_vpix,

@@ -32,7 +32,7 @@ constexpr int kStatusRange = 2;
 struct TriRaster {
     int X[3], Y[3];   // snapped vertex positions
     float zd[3];      // zeta_i / |E_0 + E_1 + E_2|, FP32
-    int flags;        // bits 0..2: edge i is top-left; bit 3: negative area; bit 31: culled
+    int flags;        // bits 0..2: edge i is top-left; bit 3: negative area; bit 4: small (32-bit path); bit 31: culled
     short bx0, bx1, by0, by1;  // inclusive pixel bounding box of the covered centres
 };
 static_assert(sizeof(TriRaster) == 48, "TriRaster");
@@ -53,6 +53,21 @@ __device__ __forceinline__ bool covers(const TriRaster& t, int px, int py, int64
         if (neg) e = -e;
         // covered iff e > 0, or e == 0 on a top-left edge: e + tl > 0
         if (e + (int64_t)((t.flags >> i) & 1) <= 0) return false;
+    }
+    return true;
+}
+
+// The same predicate for a "small" triangle (snapped bbox extent < 2^14): every factor is then below 2^15
+// in magnitude for a pixel inside the bbox, so each product fits 30 bits and the edge function 31 bits.
+__device__ __forceinline__ bool covers_small(const TriRaster& t, int px, int py, int E[3]) {
+    const bool neg = (t.flags & 8) != 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, k = (i + 2) % 3;
+        int e = (t.X[j] - px) * (t.Y[k] - py) - (t.Y[j] - py) * (t.X[k] - px);
+        if (neg) e = -e;
+        E[i] = e;
+        if (e + ((t.flags >> i) & 1) <= 0) return false;
     }
     return true;
 }
@@ -96,6 +111,21 @@ __device__ __forceinline__ float ll2f_rn(long long v) {
     return __uint_as_float((e << 23) | (m & 0x7FFFFFu) | (v < 0 ? 0x80000000u : 0u));
 }
 
+// Exact small-integer conversions on the FP32/integer pipes (the hardware conversions issue at a lower
+// rate): the float 1.5 * 2^23 + v holds v in its mantissa for |v| < 2^22.
+__device__ __forceinline__ float i2f_exact(int v) {
+    if ((unsigned)(v + (1 << 22)) < (1u << 23)) return __int_as_float(0x4B400000 + v) - 12582912.0f;
+    return __int2float_rn(v);
+}
+
+// floor(x) as an int, for |x| < 2^21 by round-to-nearest through the same bias and a correction.
+__device__ __forceinline__ int floor_i(float x) {
+    if (!(fabsf(x) < 2097152.0f)) return (int)floorf(x);
+    const float r = __fadd_rn(x, 12582912.0f);
+    const int i = __float_as_int(r) - 0x4B400000;
+    return __fsub_rn(r, 12582912.0f) > x ? i - 1 : i;
+}
+
 // Non-negative int64 -> float, exact below 2^23 with one integer add and one float subtract (the bits of
 // 2^23 + v read as a float are exactly 2^23 + v); the general conversion otherwise.
 __device__ __forceinline__ float nonneg_ll2f_rn(long long v) {
@@ -108,8 +138,56 @@ __device__ __forceinline__ float signed_ll2f_rn(long long v) {
     return v < 0 ? -f : f;
 }
 
+// covers_pts with a 32-bit path: when every |X_j - px|, |Y_j - py| < 2^15 each product fits 30 bits and each
+// edge function 31 bits; the area is their sum (taken in 64 bits).  Falls back to 64-bit arithmetic.
+__device__ __forceinline__ bool covers_xy(const int X[3], const int Y[3], int px, int py) {
+    int dx[3], dy[3];
+    bool small = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dx[i] = X[i] - px;
+        dy[i] = Y[i] - py;
+        small &= (unsigned)(dx[i] + 32768) < 65536u && (unsigned)(dy[i] + 32768) < 65536u;
+    }
+    if (!small) return covers_pts(X, Y, px, py);
+    int E[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, k = (i + 2) % 3;
+        E[i] = dx[j] * dy[k] - dy[j] * dx[k];
+    }
+    const long long a2 = (long long)E[0] + E[1] + E[2];
+    if (a2 == 0) return false;
+    const bool pos = a2 > 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int e = pos ? E[i] : -E[i];
+        if (e > 0) continue;
+        if (e < 0) return false;
+        const int j = (i + 1) % 3, k = (i + 2) % 3;
+        const int ga = pos ? (Y[j] - Y[k]) : (Y[k] - Y[j]);
+        const int gb = pos ? (X[k] - X[j]) : (X[j] - X[k]);
+        if (!(ga > 0 || (ga == 0 && gb > 0))) return false;
+    }
+    return true;
+}
+
 // FP32 depth key: sum_i E_i * (zeta_i / sum E) with correctly rounded conversions
 // and an FMA chain (relative error <= 7 * 2^-24, see the design notes).
+// Non-negative int32 -> float, correctly rounded.
+__device__ __forceinline__ float nonneg_i2f_rn(int v) {
+    if ((unsigned)v < (1u << 23)) return __uint_as_float(0x4B000000u + (unsigned)v) - 8388608.0f;
+    return __int2float_rn(v);
+}
+
+// Depth key of a small triangle from the sign-normalised 32-bit edge functions (same rounding as below).
+__device__ __forceinline__ float depth_key_small(const TriRaster& t, const int E[3]) {
+    float z = __fmul_rn(nonneg_i2f_rn(E[0]), t.zd[0]);
+    z = __fmaf_rn(nonneg_i2f_rn(E[1]), t.zd[1], z);
+    z = __fmaf_rn(nonneg_i2f_rn(E[2]), t.zd[2], z);
+    return z;
+}
+
 // zd_i = zeta_i / |sum E| and |E_i| (E_i has the sign of the area at a covered pixel), so every term is >= 0.
 __device__ __forceinline__ float depth_key(const TriRaster& t, const int64_t E[3]) {
     const bool neg = (t.flags & 8) != 0;
@@ -128,6 +206,25 @@ __device__ __forceinline__ float diff_of_products(float a, float d, float b, flo
     return f + e;
 }
 
+// A projected vertex record loaded with two 128-bit loads (records are 32-byte aligned).
+struct VRec {
+    int X, Y;
+    float rx, ry, zeta, zeta_lo;
+};
+
+__device__ __forceinline__ VRec load_vrec(const mer_vertex* p) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    const float2 b = __ldg(reinterpret_cast<const float2*>(p) + 2);
+    VRec r;
+    r.X = __float_as_int(a.x);
+    r.Y = __float_as_int(a.y);
+    r.rx = a.z;
+    r.ry = a.w;
+    r.zeta = b.x;
+    r.zeta_lo = b.y;
+    return r;
+}
+
 // Screen barycentrics of a pixel centre and their screen gradients.
 struct Bary {
     float lam[3];
@@ -140,18 +237,18 @@ struct Bary {
 //   e_i = cross(v_j - P, v_k - P) = [a_j b_k - b_j a_k] + [a_j s_k + r_j b_k - b_j r_k - s_j a_k] + [r_j s_k - s_j r_k]
 // has an exact integer first bracket (the snapped edge function / 65536), so
 // e_i is accurate to about one ulp of itself even where it is small.
-__device__ __forceinline__ Bary screen_bary(const mer_vertex* v[3], int x, int y) {
+__device__ __forceinline__ Bary screen_bary(const VRec v[3], int x, int y) {
     const int pxf = 256 * x + 128, pyf = 256 * y + 128;
     int ix[3], iy[3];
     float a[3], b[3], r[3], s[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        ix[i] = v[i]->X - pxf;
-        iy[i] = v[i]->Y - pyf;
-        a[i] = __int2float_rn(ix[i]) * (1.0f / 256.0f);
-        b[i] = __int2float_rn(iy[i]) * (1.0f / 256.0f);
-        r[i] = v[i]->rx;
-        s[i] = v[i]->ry;
+        ix[i] = v[i].X - pxf;
+        iy[i] = v[i].Y - pyf;
+        a[i] = i2f_exact(ix[i]) * (1.0f / 256.0f);
+        b[i] = i2f_exact(iy[i]) * (1.0f / 256.0f);
+        r[i] = v[i].rx;
+        s[i] = v[i].ry;
     }
     Bary B;
     float e[3];
@@ -170,8 +267,8 @@ __device__ __forceinline__ Bary screen_bary(const mer_vertex* v[3], int x, int y
         const int j = (i + 1) % 3, k = (i + 2) % 3;
         B.lam[i] = e[i] * inv;
         // dy_j - dy_k and dx_k - dx_j from exact integer differences plus residuals
-        B.gx[i] = (__int2float_rn(iy[j] - iy[k]) * (1.0f / 256.0f) + (s[j] - s[k])) * inv;
-        B.gy[i] = (__int2float_rn(ix[k] - ix[j]) * (1.0f / 256.0f) + (r[k] - r[j])) * inv;
+        B.gx[i] = (i2f_exact(iy[j] - iy[k]) * (1.0f / 256.0f) + (s[j] - s[k])) * inv;
+        B.gy[i] = (i2f_exact(ix[k] - ix[j]) * (1.0f / 256.0f) + (r[k] - r[j])) * inv;
     }
     return B;
 }
@@ -196,11 +293,12 @@ __device__ __forceinline__ TexCoord tex_coord(float u0, float u1, float u2, floa
     const float Nf = (float)N;
     const float xb = u0 * Nf - 0.5f;
     const float d = b1 * ((u1 * Nf - 0.5f) - xb) + b2 * ((u2 * Nf - 0.5f) - xb);
-    const float fl = floorf(xb);
+    const int fli = floor_i(xb);
+    const float fl = i2f_exact(fli);
     const float f = (xb - fl) + d;  // xb - fl is exact
-    const float c = floorf(f);
-    float fr = f - c;
-    int cell = (int)fl + (int)c;
+    const int ci = floor_i(f);
+    float fr = f - i2f_exact(ci);
+    int cell = fli + ci;
     if (fr >= 1.0f) {  // f just below an integer rounded up: the next cell at fraction 0
         fr = 0.0f;
         cell += 1;
@@ -220,8 +318,12 @@ struct TexTaps {
 
 __device__ __forceinline__ TexTaps tex_taps(int TH, int TW, TexCoord cx, TexCoord cy) {
     TexTaps t;
-    t.i0 = cx.cell % TW;
-    if (t.i0 < 0) t.i0 += TW;
+    if ((unsigned)cx.cell < (unsigned)TW) {
+        t.i0 = cx.cell;
+    } else {
+        t.i0 = cx.cell % TW;
+        if (t.i0 < 0) t.i0 += TW;
+    }
     t.i1 = (t.i0 + 1 == TW) ? 0 : t.i0 + 1;
     t.fx = cx.frac;
     t.clamped = false;
@@ -235,31 +337,79 @@ __device__ __forceinline__ TexTaps tex_taps(int TH, int TW, TexCoord cx, TexCoor
     return t;
 }
 
-// Bilinear value of channel c.
-__device__ __forceinline__ float tex_value(const float* __restrict__ tex, int TW, int nc, const TexTaps& t, int c) {
-    const float* r0 = tex + (size_t)t.j0 * TW * nc;
-    const float* r1 = tex + (size_t)t.j1 * TW * nc;
-    const float t00 = __ldg(r0 + (size_t)t.i0 * nc + c), t10 = __ldg(r0 + (size_t)t.i1 * nc + c);
-    const float t01 = __ldg(r1 + (size_t)t.i0 * nc + c), t11 = __ldg(r1 + (size_t)t.i1 * nc + c);
-    const float a = t00 + t.fx * (t10 - t00);
-    const float b = t01 + t.fx * (t11 - t01);
-    return a + t.fy * (b - a);
+// Texel (j, i) of a texture with `stride` floats per texel; vec4: stride == 4 and 16-byte aligned (one
+// 128-bit load per texel).
+__device__ __forceinline__ float4 texel4(const float* __restrict__ tex, int TW, int stride, bool vec4, int nc, int j,
+                                         int i) {
+    const float* q = tex + ((size_t)j * TW + i) * stride;
+    if (vec4) return __ldg(reinterpret_cast<const float4*>(q));
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.x = __ldg(q);
+    if (nc > 1) r.y = __ldg(q + 1);
+    if (nc > 2) r.z = __ldg(q + 2);
+    if (nc > 3) r.w = __ldg(q + 3);
+    return r;
+}
+
+__device__ __forceinline__ float comp(const float4& v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
+
+// Bilinear values of channels 0..nc-1 written to out[0..nc-1].
+__device__ __forceinline__ void tex_values(const float* __restrict__ tex, int TW, int stride, bool vec4, int nc,
+                                           const TexTaps& t, float* out) {
+    if (nc <= 4) {
+        const float4 a00 = texel4(tex, TW, stride, vec4, nc, t.j0, t.i0), a10 = texel4(tex, TW, stride, vec4, nc, t.j0, t.i1);
+        const float4 a01 = texel4(tex, TW, stride, vec4, nc, t.j1, t.i0), a11 = texel4(tex, TW, stride, vec4, nc, t.j1, t.i1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (c >= nc) break;
+            const float t00 = comp(a00, c), t10 = comp(a10, c), t01 = comp(a01, c), t11 = comp(a11, c);
+            const float a = t00 + t.fx * (t10 - t00);
+            const float b = t01 + t.fx * (t11 - t01);
+            out[c] = a + t.fy * (b - a);
+        }
+        return;
+    }
+    const float* r0 = tex + (size_t)t.j0 * TW * stride;
+    const float* r1 = tex + (size_t)t.j1 * TW * stride;
+    for (int c = 0; c < nc; ++c) {
+        const float t00 = __ldg(r0 + (size_t)t.i0 * stride + c), t10 = __ldg(r0 + (size_t)t.i1 * stride + c);
+        const float t01 = __ldg(r1 + (size_t)t.i0 * stride + c), t11 = __ldg(r1 + (size_t)t.i1 * stride + c);
+        const float a = t00 + t.fx * (t10 - t00);
+        const float b = t01 + t.fx * (t11 - t01);
+        out[c] = a + t.fy * (b - a);
+    }
 }
 
 // sum_c g_c dT_c/du and sum_c g_c dT_c/dv (g read from global memory, nc channels).
-__device__ __forceinline__ void tex_grad_uv(const float* __restrict__ tex, int TH, int TW, int nc, const TexTaps& t,
-                                            const float* __restrict__ g, float& gu, float& gv) {
-    const float* r0 = tex + (size_t)t.j0 * TW * nc;
-    const float* r1 = tex + (size_t)t.j1 * TW * nc;
+__device__ __forceinline__ void tex_grad_uv(const float* __restrict__ tex, int TH, int TW, int stride, bool vec4,
+                                            int nc, const TexTaps& t, const float* __restrict__ g, float& gu,
+                                            float& gv) {
     float su = 0.f, sv = 0.f;
-    for (int c = 0; c < nc; ++c) {
-        const float t00 = __ldg(r0 + (size_t)t.i0 * nc + c), t10 = __ldg(r0 + (size_t)t.i1 * nc + c);
-        const float t01 = __ldg(r1 + (size_t)t.i0 * nc + c), t11 = __ldg(r1 + (size_t)t.i1 * nc + c);
-        const float gc = __ldg(g + c);
-        su += gc * ((1.0f - t.fy) * (t10 - t00) + t.fy * (t11 - t01));
-        const float a = t00 + t.fx * (t10 - t00);
-        const float b = t01 + t.fx * (t11 - t01);
-        sv += gc * (b - a);
+    if (nc <= 4) {
+        const float4 a00 = texel4(tex, TW, stride, vec4, nc, t.j0, t.i0), a10 = texel4(tex, TW, stride, vec4, nc, t.j0, t.i1);
+        const float4 a01 = texel4(tex, TW, stride, vec4, nc, t.j1, t.i0), a11 = texel4(tex, TW, stride, vec4, nc, t.j1, t.i1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (c >= nc) break;
+            const float t00 = comp(a00, c), t10 = comp(a10, c), t01 = comp(a01, c), t11 = comp(a11, c);
+            const float gc = __ldg(g + c);
+            su += gc * ((1.0f - t.fy) * (t10 - t00) + t.fy * (t11 - t01));
+            const float a = t00 + t.fx * (t10 - t00);
+            const float b = t01 + t.fx * (t11 - t01);
+            sv += gc * (b - a);
+        }
+    } else {
+        const float* r0 = tex + (size_t)t.j0 * TW * stride;
+        const float* r1 = tex + (size_t)t.j1 * TW * stride;
+        for (int c = 0; c < nc; ++c) {
+            const float t00 = __ldg(r0 + (size_t)t.i0 * stride + c), t10 = __ldg(r0 + (size_t)t.i1 * stride + c);
+            const float t01 = __ldg(r1 + (size_t)t.i0 * stride + c), t11 = __ldg(r1 + (size_t)t.i1 * stride + c);
+            const float gc = __ldg(g + c);
+            su += gc * ((1.0f - t.fy) * (t10 - t00) + t.fy * (t11 - t01));
+            const float a = t00 + t.fx * (t10 - t00);
+            const float b = t01 + t.fx * (t11 - t01);
+            sv += gc * (b - a);
+        }
     }
     gu = (float)TW * su;
     gv = t.clamped ? 0.0f : (float)TH * sv;

@@ -80,6 +80,7 @@ __global__ void k_setup_count(const mer_vertex* __restrict__ vpix, const int* __
         const int64_t gb = (int64_t)s * (r.X[k] - r.X[j]);
         if (ga > 0 || (ga == 0 && gb > 0)) fl |= 1 << e;
     }
+    if (mxx - mnx < (1 << 14) && mxy - mny < (1 << 14)) fl |= 16;  // small: exact 32-bit coverage
     r.flags = fl;
     const float Df = ll2f_rn(a2 < 0 ? -a2 : a2);
 #pragma unroll
@@ -222,15 +223,29 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(const TriRaster* __re
             const int bw = x1 - x0 + 1, bh = y1 - y0 + 1;
             if (bw <= 0 || bh <= 0) continue;
             const int npx = bw * bh;
-            const float inv_bw = 1.0f / (float)bw;
             const unsigned idkey = 0xFFFFFFFFu - (unsigned)sh_id[j];
+            // lane -> (dx, dy) in the bbox, then advance by 32 pixels per pass without dividing per pixel
+            int dy = lane / bw;
+            int dx = lane - dy * bw;
+            const int sy = 32 / bw, sx = 32 - sy * bw;
             for (int i = lane; i < npx; i += 32) {
-                const int dy = (int)(((float)i + 0.5f) * inv_bw);  // exact: the fraction stays >= 1/(2 bw)
-                const int dx = i - dy * bw;
                 const int px = x0 + dx, py = y0 + dy;
-                int64_t E[3];
-                if (!covers(r, 256 * px + 128, 256 * py + 128, E)) continue;
-                const float z = depth_key(r, E);
+                dx += sx;
+                dy += sy;
+                if (dx >= bw) {
+                    dx -= bw;
+                    ++dy;
+                }
+                float z;
+                if (r.flags & 16) {
+                    int E[3];
+                    if (!covers_small(r, 256 * px + 128, 256 * py + 128, E)) continue;
+                    z = depth_key_small(r, E);
+                } else {
+                    int64_t E[3];
+                    if (!covers(r, 256 * px + 128, 256 * py + 128, E)) continue;
+                    z = depth_key(r, E);
+                }
                 const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | idkey;
                 atomicMax(&zbuf[(py - oy) * TS + (px - ox)], key);
             }
@@ -248,9 +263,10 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(const TriRaster* __re
         if (!depth && !bary) continue;
         float Z = 0.f, b1 = 0.f, b2 = 0.f;
         if (t >= 0) {
-            const mer_vertex* v[3] = {vb + tris[3 * (size_t)t], vb + tris[3 * (size_t)t + 1], vb + tris[3 * (size_t)t + 2]};
+            const VRec v[3] = {load_vrec(vb + tris[3 * (size_t)t]), load_vrec(vb + tris[3 * (size_t)t + 1]),
+                               load_vrec(vb + tris[3 * (size_t)t + 2])};
             const Bary B = screen_bary(v, px, py);
-            const float z0 = v[0]->zeta, z1 = v[1]->zeta, z2 = v[2]->zeta;
+            const float z0 = v[0].zeta, z1 = v[1].zeta, z2 = v[2].zeta;
             const float s = B.lam[0] * z0 + B.lam[1] * z1 + B.lam[2] * z2;
             const float is = 1.0f / s;
             Z = is;

@@ -6,6 +6,8 @@
 // texture, coverage mask, depth) as one contiguous NHWC run per pixel.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "mer_device.cuh"
 
 namespace mer {
@@ -13,6 +15,8 @@ namespace mer {
 struct ShadeArgs {
     mer_shading sh;
     float bg[kMaxC];
+    int tex_stride;  // floats per texel
+    bool tex_vec4;   // stride 4 and 16-byte aligned: 128-bit texel loads
 };
 
 __global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* __restrict__ tris, int T, int n, int H,
@@ -22,56 +26,70 @@ __global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* _
     const long long npix = (long long)n * H * W;
     if (p >= npix) return;
     const int C = a.sh.C;
-    float out[kMaxC];
-#pragma unroll
-    for (int c = 0; c < kMaxC; ++c) out[c] = c < C ? a.bg[c] : 0.f;
+    float* o = image + (size_t)p * C;
     const int t = index[p];
     if (t >= T) set_status(ws, kStatusRange);
-    if (t >= 0 && t < T) {
-        const int view = (int)(p / ((long long)H * W));
-        const int rem = (int)(p % ((long long)H * W));
-        const int y = rem / W, x = rem % W;
-        const mer_vertex* vb = vpix + (size_t)view * V;
-        const int i0 = tris[3 * (size_t)t], i1 = tris[3 * (size_t)t + 1], i2 = tris[3 * (size_t)t + 2];
+    int i0 = 0, i1 = 0, i2 = 0;
+    bool ok = t >= 0 && t < T;
+    if (ok) {
+        i0 = tris[3 * (size_t)t];
+        i1 = tris[3 * (size_t)t + 1];
+        i2 = tris[3 * (size_t)t + 2];
         if ((unsigned)i0 >= (unsigned)V || (unsigned)i1 >= (unsigned)V || (unsigned)i2 >= (unsigned)V) {
             set_status(ws, kStatusRange);
-            return;
+            ok = false;
         }
-        const mer_vertex* v[3] = {vb + i0, vb + i1, vb + i2};
-        const int vid[3] = {i0, i1, i2};
-        const Bary B = screen_bary(v, x, y);
-        float b[3];
-        const float s = B.lam[0] * v[0]->zeta + B.lam[1] * v[1]->zeta + B.lam[2] * v[2]->zeta;
-        const float is = 1.0f / s;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) b[k] = B.lam[k] * v[k]->zeta * is;
-        const int Ca = a.sh.C_attr;
-        if (a.sh.uv_offset < 0) {
-            for (int c = 0; c < a.sh.n_main; ++c) {
-                float acc = 0.f;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) acc += b[k] * __ldg(attr + (size_t)vid[k] * Ca + c);
-                out[c] = acc;
-            }
-        } else {
-            float uk[3], vk[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                uk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset);
-                vk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1);
-            }
-            const TexCoord cx = tex_coord(uk[0], uk[1], uk[2], b[1], b[2], a.sh.tex_w);
-            const TexCoord cy = tex_coord(vk[0], vk[1], vk[2], b[1], b[2], a.sh.tex_h);
-            const TexTaps taps = tex_taps(a.sh.tex_h, a.sh.tex_w, cx, cy);
-            for (int c = 0; c < a.sh.n_main && c < kMaxC; ++c) out[c] = tex_value(tex, a.sh.tex_w, a.sh.n_main, taps, c);
-        }
-        if (a.sh.mask_ch >= 0) out[a.sh.mask_ch] = 1.0f;
-        if (a.sh.depth_ch >= 0) out[a.sh.depth_ch] = is;
     }
-    float* o = image + (size_t)p * C;
+    if (!ok) {
 #pragma unroll
-    for (int c = 0; c < kMaxC; ++c)
-        if (c < C) o[c] = out[c];
+        for (int c = 0; c < kMaxC; ++c)  // static indices keep the arguments out of local memory
+            if (c < C) o[c] = a.bg[c];
+        return;
+    }
+    const int view = (int)(p / ((long long)H * W));
+    const int rem = (int)(p % ((long long)H * W));
+    const int y = rem / W, x = rem % W;
+    const mer_vertex* vb = vpix + (size_t)view * V;
+    const VRec v[3] = {load_vrec(vb + i0), load_vrec(vb + i1), load_vrec(vb + i2)};
+    const int vid[3] = {i0, i1, i2};
+    const Bary B = screen_bary(v, x, y);
+    float b[3];
+    const float s = B.lam[0] * v[0].zeta + B.lam[1] * v[1].zeta + B.lam[2] * v[2].zeta;
+    const float is = 1.0f / s;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b[k] = B.lam[k] * v[k].zeta * is;
+    const int Ca = a.sh.C_attr;
+    if (a.sh.uv_offset < 0) {
+        for (int c = 0; c < a.sh.n_main; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc += b[k] * __ldg(attr + (size_t)vid[k] * Ca + c);
+            o[c] = acc;
+        }
+    } else {
+        float uk[3], vk[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset);
+            vk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1);
+        }
+        const TexCoord cx = tex_coord(uk[0], uk[1], uk[2], b[1], b[2], a.sh.tex_w);
+        const TexCoord cy = tex_coord(vk[0], vk[1], vk[2], b[1], b[2], a.sh.tex_h);
+        const TexTaps taps = tex_taps(a.sh.tex_h, a.sh.tex_w, cx, cy);
+        if (a.sh.n_main <= 4) {
+            float v4[4];
+            tex_values(tex, a.sh.tex_w, a.tex_stride, a.tex_vec4, a.sh.n_main, taps, v4);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < a.sh.n_main) o[c] = v4[c];
+        } else {
+            float vk_[kMaxC];
+            tex_values(tex, a.sh.tex_w, a.tex_stride, false, a.sh.n_main, taps, vk_);
+            for (int c = 0; c < a.sh.n_main && c < kMaxC; ++c) o[c] = vk_[c];
+        }
+    }
+    if (a.sh.mask_ch >= 0) o[a.sh.mask_ch] = 1.0f;
+    if (a.sh.depth_ch >= 0) o[a.sh.depth_ch] = is;
 }
 
 }  // namespace mer
@@ -86,6 +104,8 @@ extern "C" int mer_launch_shade(const mer_vertex* vpix, int V, const int* tris, 
     ShadeArgs a;
     a.sh = *sh;
     for (int c = 0; c < kMaxC; ++c) a.bg[c] = (bg && c < sh->C) ? bg[c] : 0.f;
+    a.tex_stride = sh->tex_c > 0 ? sh->tex_c : sh->n_main;
+    a.tex_vec4 = a.tex_stride == 4 && tex && (reinterpret_cast<uintptr_t>(tex) & 15u) == 0;
     k_shade<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(vpix, V, tris, T, n, H, W, index, attr, tex, a, image, ws);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

@@ -33,6 +33,7 @@ class Renderer:
         self.sh = B.shading_struct(shading, C_attr, None)
         if tex_shape is not None:
             self.sh.tex_h, self.sh.tex_w = int(tex_shape[0]), int(tex_shape[1])
+            self.sh.tex_c = int(tex_shape[2]) if len(tex_shape) > 2 else shading.n_main
         self.bg = shading.bg_array()
         n, H, W = self.n, self.H, self.W
         self.vpix = torch.empty((n, self.V, B.VERTEX_FLOATS), dtype=torch.float32, device=device)

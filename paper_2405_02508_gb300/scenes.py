@@ -212,6 +212,13 @@ def vertex_normals(V: np.ndarray, F: np.ndarray) -> np.ndarray:
     return vn / np.maximum(np.linalg.norm(vn, axis=1, keepdims=True), 1e-30)
 
 
+def padded_rgba(tex: np.ndarray) -> np.ndarray:
+    """[H, W, 3] -> [H, W, 4] with a zero fourth channel: texels 16 bytes apart, for 128-bit loads."""
+    out = np.zeros(tex.shape[:2] + (4,), np.float32)
+    out[..., : tex.shape[2]] = tex
+    return out
+
+
 def noise_texture(size: int, channels: int, seed: int, sigma: float = 4.0) -> np.ndarray:
     """Uniform noise blurred by a wrapping Gaussian of ``sigma`` texels, rescaled to [0, 1] per channel."""
     rng = np.random.default_rng(seed)
@@ -262,7 +269,7 @@ class Scene:
     W: int
     attr: np.ndarray           # [V,C_a] float32
     shading: Shading
-    tex: np.ndarray | None = None   # [TH,TW,n_main] float32
+    tex: np.ndarray | None = None   # [TH,TW,tex_c >= n_main] float32
     upstream_seed: int = 0
     target_verts: np.ndarray | None = None
 
@@ -325,7 +332,7 @@ def head_mesh(n: int = 128, seed: int = 4):
 def head_single_view(H: int = 1024, W: int = 1024, n: int = 128, tex_size: int = 1024) -> Scene:
     """Head-scale single view: textured displaced sphere, RGB + mask, camera at distance 3."""
     V, F, uv = head_mesh(n)
-    tex = noise_texture(tex_size, 3, seed=5)
+    tex = padded_rgba(noise_texture(tex_size, 3, seed=5))
     cams = np.stack([look_at_camera((0.0, 0.0, 3.0), H, W)])
     sh = Shading(n_main=3, C=4, uv_offset=0, mask_ch=3, bg=[0, 0, 0, 0])
     return Scene(f"head_{H}x{W}", V, F, cams, H, W, uv, sh, tex=tex, upstream_seed=10)
@@ -335,7 +342,7 @@ def head_multiview(n_views: int = 32, H: int = 2048, W: int = 1334, n: int = 128
                    tex_size: int = 1024, seed: int = 6) -> Scene:
     """Multi-view head: the head mesh seen by ``n_views`` cameras at radius 3, RGB + mask + depth."""
     V, F, uv = head_mesh(n)
-    tex = noise_texture(tex_size, 3, seed=5)
+    tex = padded_rgba(noise_texture(tex_size, 3, seed=5))
     cams = cameras_on_sphere(n_views, 3.0, H, W, seed)
     sh = Shading(n_main=3, C=5, uv_offset=0, mask_ch=3, depth_ch=4, bg=[0, 0, 0, 0, 0])
     return Scene(f"head_{n_views}x{W}x{H}", V, F, cams, H, W, uv, sh, tex=tex, upstream_seed=7)
