@@ -31,12 +31,13 @@ METRIC = "raster+micro-edge backward Mpix/s on 1 GB300; % HBM roofline; batched 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tile", type=int, default=32)
+    ap.add_argument("--tile", type=int, default=0, help="bin tile; 0 = autotune over 16/32/64")
     ap.add_argument("--views", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the per-view launch path")
     return ap.parse_args()
 
 
@@ -50,7 +51,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples every 50 ms while the timed region runs."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -64,7 +65,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -182,7 +183,7 @@ def main():
 
     from paper_2405_02508_gb300 import binding as B
     from paper_2405_02508_gb300 import scenes
-    from paper_2405_02508_gb300.render import Renderer
+    from paper_2405_02508_gb300.batch import BatchRenderer, PlainRenderer, autotune_tile, workload_key
 
     B.lib()
     dev = "cuda"
@@ -191,43 +192,31 @@ def main():
     n, H, W, C = scene.n_views, scene.H, scene.W, scene.shading.C
     V, T = len(scene.verts), len(scene.tris)
     verts = torch.from_numpy(scene.verts).to(dev)
-    cams = B.cameras_tensor(scene.cams)
     attr = torch.from_numpy(scene.attr).to(dev)
     tex = torch.from_numpy(scene.tex).to(dev)
     gen = torch.Generator(device=dev)
     gen.manual_seed(7 + rank)
-    g = torch.randn((n, H, W, C), generator=gen, device=dev, dtype=torch.float32)
-    r = Renderer(torch.from_numpy(scene.tris), V, n, H, W, scene.shading, attr.shape[1], tex.shape, tile=args.tile)
-    r.forward(verts, cams, attr, tex, checked=True)  # sizes the bin list once
+    g = torch.randn((n * H * W, C), generator=gen, device=dev, dtype=torch.float32)
+    meshes = [(scene.verts, scene.tris)]
+    items = [(0, v, H, W) for v in range(n)]
     stream = torch.cuda.current_stream()
 
-    ev_b0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_b1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_r0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev_r1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    def make(tile):
+        br = BatchRenderer(meshes, items, scene.cams, scene.shading, attr.shape[1], tex, tile=tile)
+        br.prepare(verts, attr, tex)
+        return br
 
-    def step(i=None):
-        if i is not None:
-            ev_r0[i].record(stream)
-        r.project(verts, cams)
-        r.rasterize(checked=False)
-        if i is not None:
-            ev_r1[i].record(stream)
-        r.shade(attr, tex)
-        r.grad_vpix.zero_()
-        r.grad_verts.zero_()
-        if i is not None:
-            ev_b0[i].record(stream)
-        B.mer_backward(r.vpix, r.tris, r.index, r.image, g, attr, tex, r.sh, B.MER_EDGE | B.MER_INTERIOR |
-                       B.MER_INTERSECT, r.grad_vpix, None, r.workspace)
-        if i is not None:
-            ev_b1[i].record(stream)
-        B.mer_project_backward(cams, r.vpix, r.grad_vpix, r.grad_verts)
+    if args.tile > 0:
+        tile, tune = args.tile, {}
+    else:  # autotuned bin tile, cached per workload signature
+        tile, tune = autotune_tile(make, lambda r: r.step(verts, attr, g, tex), key=workload_key(items, meshes))
+    br = make(tile)
+    br.capture(verts, attr, g, tex)  # one CUDA graph: the whole forward + backward step
 
     for _ in range(args.warmup):
-        step()
-    r.check_status()
+        br.replay()
     torch.cuda.synchronize()
+    br.check()
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
@@ -236,26 +225,43 @@ def main():
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for i in range(args.steps):
-        step(i)
+    for _ in range(args.steps):
+        br.replay()
     t1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    r.check_status()
+    br.check()
     ms = t0.elapsed_time(t1) / args.steps
     if world > 1:
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    bwd_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(ev_b0, ev_b1)]))
-    ras_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(ev_r0, ev_r1)]))
 
-    # end-to-end: host vertex positions in, host vertex gradients out, copies inside the timed region
+    # per-kernel times: the same step run eagerly with CUDA events around the stages on the launching stream
+    ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)] for k in ("fwd", "bwd", "rast")}
+    for i in range(args.steps):
+        ev["fwd"][2 * i].record(stream)
+        B.mer_batch_project(verts, br.cams, br.items, br.tot, br.vpix)
+        ev["rast"][2 * i].record(stream)
+        B.mer_batch_rasterize(br.vpix, br.tris, br.items, br.tot, br.workspace, br.index, None, None, br.persistent_ctas)
+        ev["rast"][2 * i + 1].record(stream)
+        B.mer_batch_shade(br.vpix, br.tris, br.items, br.tot, br.index, attr, tex, br.bg, br.sh, br.image, br.workspace)
+        ev["fwd"][2 * i + 1].record(stream)
+        br.grad_vpix.zero_()
+        br.grad_verts.zero_()
+        ev["bwd"][2 * i].record(stream)
+        B.mer_batch_backward(br.vpix, br.tris, br.items, br.tot, br.index, br.image, g, attr, tex, br.sh, 7,
+                             br.grad_vpix, None, br.workspace, br.persistent_ctas)
+        ev["bwd"][2 * i + 1].record(stream)
+        B.mer_batch_project_backward(br.cams, br.items, br.tot, br.vpix, br.grad_vpix, br.grad_verts)
+    torch.cuda.synchronize()
+    kms = {k: float(np.mean([e[2 * i].elapsed_time(e[2 * i + 1]) for i in range(args.steps)])) for k, e in ev.items()}
+
+    # end-to-end through the public API: host vertex positions in, host vertex gradients out, per step
     h_verts = torch.from_numpy(scene.verts).pin_memory()
     h_grad = torch.empty((V, 3), dtype=torch.float32).pin_memory()
-    d_verts = torch.empty_like(verts)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -263,15 +269,9 @@ def main():
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
-        d_verts.copy_(h_verts, non_blocking=True)
-        r.project(d_verts, cams)
-        r.rasterize(checked=False)
-        r.shade(attr, tex)
-        r.grad_vpix.zero_()
-        r.grad_verts.zero_()
-        B.mer_backward(r.vpix, r.tris, r.index, r.image, g, attr, tex, r.sh, 7, r.grad_vpix, None, r.workspace)
-        B.mer_project_backward(cams, r.vpix, r.grad_vpix, r.grad_verts)
-        h_grad.copy_(r.grad_verts, non_blocking=True)
+        verts.copy_(h_verts, non_blocking=True)  # the graph reads `verts` in place
+        br.replay()
+        h_grad.copy_(br.grad_verts[:V], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
@@ -280,25 +280,46 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
 
+    # plain path: each view its own launch sequence (same kernels, no batching, no graph)
+    plain_ms = None
+    if not args.no_plain:
+        pr = PlainRenderer(meshes, items, scene.cams, scene.shading, attr.shape[1], tex.shape, tile=32)
+        gv = [g[k * H * W:(k + 1) * H * W].view(1, H, W, C) for k in range(n)]
+        pr.step([verts], [attr], gv, tex, checked=True)
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(max(1, args.steps // 2)):
+            pr.step([verts], [attr], gv, tex)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = p0.elapsed_time(p1) / max(1, args.steps // 2)
+        del pr
+
     px_step = n * H * W * world
     value = px_step / (ms * 1e-3) / 1e6
     peak, peak_kind = peaks()
     bb = backward_bytes_per_launch(n, H, W, C, V)
-    achieved = bb / (bwd_ms * 1e-3) / 1e9
-    launches_per_step = 10  # project 1, binning+scan+raster 6, shade 1, backward 1, projection backward 1
+    achieved = bb / (kms["bwd"] * 1e-3) / 1e9
+    launches_per_step = 10  # project 1, setup/count 1, scan 3, fill 1, raster 1, shade 1, backward 1, proj. backward 1
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"head multi-view: {n} views x {W}x{H}, {V} verts / {T} tris, 1024^2 texture, "
                                f"RGB+mask+depth (C={C}), upstream N(0,1)", "views_per_gpu": n, "H": H, "W": W,
-                   "triangles": T, "tile": args.tile, "l2": "inputs larger than L2 (images 1.7 GB per step)",
-                   "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": "k_backward (fused edge + interior)", "achieved": achieved,
+                   "triangles": T, "path": "batched: persistent raster/backward over a device tile queue, "
+                   "one CUDA graph per step", "tile": tile, "tile_autotune_ms": tune,
+                   "l2": "inputs larger than L2 (images 1.7 GB per step)", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": "k_backward_batch (fused edge + interior)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "peak_kind": peak_kind, "kernel_ms": bwd_ms, "algorithmic_bytes": bb},
-        "kernels_ms": {"project+bin+raster": ras_ms, "backward": bwd_ms},
+                     "peak_kind": peak_kind, "kernel_ms": kms["bwd"], "algorithmic_bytes": bb},
+        "kernels_ms": {"forward (project+raster+shade)": kms["fwd"], "bin+raster": kms["rast"],
+                       "backward": kms["bwd"]},
         "step_algorithmic_gbs": step_bytes(n, H, W, C, V, T, tex.numel() * 4) / (ms * 1e-3) / 1e9,
+        "plain": None if plain_ms is None else {"value": px_step / (plain_ms * 1e-3) / 1e6, "unit": "Mpix/s",
+                                                "ms_per_step": plain_ms, "launches_per_step": 10 * n},
         "e2e": {"value": px_step / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": V * 12,
                 "d2h_bytes_per_step": V * 12, "ms_per_step": e2e_ms},
         "gpu_launches": launches_per_step * args.steps,

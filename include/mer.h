@@ -201,6 +201,67 @@ int mer_interpolate_backward(const float* attr, int C_attr, const int32_t* tris,
 int mer_project_backward(int V, const mer_camera* cams, int n, const mer_vertex* vpix, const double* grad_vpix,
                          float* grad_verts, void* stream);
 
+/* ------------------------------------------------------------------------------------------------
+ * Batched path: many items (a mesh seen by one camera) of uneven triangle counts and image sizes in
+ * one launch per stage.  The raster and the backward run as persistent kernels whose CTAs (a whole
+ * number of waves of the SM count) take bin / backward tiles of all items from a device work queue,
+ * so large and small items balance; a caller can capture the whole step in one CUDA graph.
+ *
+ * Items index concatenated buffers.  The caller fills V, T, H, W, cam, vert and tri (several items may
+ * share a mesh: same vert / tri, e.g. the views of one object); mer_batch_plan fills the other offsets
+ * (every item gets its own vertex records, raster records, pixels and tiles) and the totals.
+ *   verts / attr / grad_verts / grad_attr rows: item.vert + local vertex id
+ *   tris: rows item.tri .. item.tri + T - 1, holding item-local vertex ids 0..V-1
+ *   vpix / grad_vpix rows: item.vrec + local vertex id
+ *   index / depth / image / grad_image / bary pixels: item.pix + y * W + x
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct mer_item {
+    int V, T, H, W;   /* vertices, triangles, image height and width */
+    int cam;          /* camera of the item (index into the camera array) */
+    int pad;
+    int64_t vert;     /* first world vertex / attribute row (set by the caller) */
+    int64_t tri;      /* first triangle row (set by the caller) */
+    int64_t vrec;     /* first vertex record (mer_batch_plan) */
+    int64_t trec;     /* first raster record (mer_batch_plan) */
+    int64_t pix;      /* first pixel (mer_batch_plan) */
+    int64_t tile;     /* first bin tile (mer_batch_plan) */
+    int64_t btile;    /* first backward tile (mer_batch_plan) */
+} mer_item;
+
+typedef struct mer_batch_totals {
+    int64_t vrecs, trecs, pixels, tiles, btiles;
+    int n_items, tile;
+} mer_batch_totals;
+
+/* Host-only: fills the offsets of items[0..n) (host array) for bin tile `tile` (16, 32 or 64) and the
+ * totals.  Returns MER_EINVAL on bad sizes (H, W > 8192, totals beyond 2^31 pixels or records). */
+int mer_batch_plan(mer_item* items, int n_items, int tile, mer_batch_totals* totals);
+
+/* Workspace bytes of mer_batch_rasterize (bin_capacity 0: 4 * trecs + 2 * tiles + 1024). */
+size_t mer_batch_workspace_size(const mer_batch_totals* totals, int64_t bin_capacity);
+
+/* Batched counterparts of the calls above; `items` is the planned table in device memory, `totals`
+ * a host pointer.  persistent_ctas: CTAs of the persistent raster and backward (0 = as many as fit
+ * on the device at once). */
+int mer_batch_project(const float* verts, const mer_camera* cams, const mer_item* items,
+                      const mer_batch_totals* totals, mer_vertex* vpix, void* stream);
+int mer_batch_rasterize(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,
+                        const mer_batch_totals* totals, void* workspace, size_t workspace_bytes,
+                        int32_t* index, float* depth, float* bary, int persistent_ctas, void* stream);
+int mer_batch_shade(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,
+                    const mer_batch_totals* totals, const int32_t* index, const float* attr, const float* tex,
+                    const float* bg_host, const mer_shading* shading_host, float* image, void* status_ws,
+                    void* stream);
+int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,
+                       const mer_batch_totals* totals, const int32_t* index, const float* image,
+                       const float* grad_image, const float* attr, const float* tex,
+                       const mer_shading* shading_host, int terms, double* grad_vpix, float* grad_attr,
+                       void* workspace, int persistent_ctas, void* stream);
+/* grad_verts [rows of all items' meshes, 3] (+=): items sharing a mesh add into the same rows. */
+int mer_batch_project_backward(const mer_camera* cams, const mer_item* items, const mer_batch_totals* totals,
+                               const mer_vertex* vpix, const double* grad_vpix, float* grad_verts,
+                               void* stream);
+
 /* Synchronises `stream`, reads and clears the device status word of a
  * workspace (or of a status buffer of at least 256 bytes passed as status_ws to
  * the other calls).  Returns MER_OK, MER_EOVERFLOW or MER_ERANGE; *total_bins

@@ -33,6 +33,19 @@ class MerShading(ctypes.Structure):
                 ("tex_h", ctypes.c_int), ("tex_w", ctypes.c_int), ("tex_c", ctypes.c_int)]
 
 
+class MerItem(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_int), ("T", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("cam", ctypes.c_int), ("pad", ctypes.c_int), ("vert", ctypes.c_int64), ("tri", ctypes.c_int64),
+                ("vrec", ctypes.c_int64), ("trec", ctypes.c_int64), ("pix", ctypes.c_int64),
+                ("tile", ctypes.c_int64), ("btile", ctypes.c_int64)]
+
+
+class MerBatchTotals(ctypes.Structure):
+    _fields_ = [("vrecs", ctypes.c_int64), ("trecs", ctypes.c_int64), ("pixels", ctypes.c_int64),
+                ("tiles", ctypes.c_int64), ("btiles", ctypes.c_int64), ("n_items", ctypes.c_int),
+                ("tile", ctypes.c_int)]
+
+
 # (name, argtypes, restype); P = pointer, I = int, Z = size_t, L = int64
 _P, _I, _Z, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_int64
 _SIGS = {
@@ -50,6 +63,15 @@ _SIGS = {
     "mer_project_backward": ([_I, _P, _I, _P, _P, _P, _P], _I),
     "mer_sync_status": ([_P, ctypes.POINTER(ctypes.c_int64), _P], _I),
     "mer_rasterize_noalloc": ([_P, _I, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P], _I),
+    "mer_batch_plan": ([_P, _I, _I, ctypes.POINTER(MerBatchTotals)], _I),
+    "mer_batch_workspace_size": ([ctypes.POINTER(MerBatchTotals), _L], _Z),
+    "mer_batch_project": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _P], _I),
+    "mer_batch_rasterize": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _Z, _P, _P, _P, _I, _P], _I),
+    "mer_batch_shade": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P, ctypes.POINTER(MerShading), _P,
+                         _P, _P], _I),
+    "mer_batch_backward": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P, _P,
+                            ctypes.POINTER(MerShading), _I, _P, _P, _P, _I, _P], _I),
+    "mer_batch_project_backward": ([_P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P], _I),
 }
 
 _lib = None
@@ -201,3 +223,51 @@ def mer_rasterize_noalloc(vpix, tris, H, W, tile, index, depth=None, bary=None, 
     n, V = vpix.shape[0], vpix.shape[1]
     _check(lib().mer_rasterize_noalloc(_ptr(vpix), V, _ptr(tris), tris.shape[0], n, H, W, tile, _ptr(index),
                                        _ptr(depth), _ptr(bary), _ptr(status), _stream()), "mer_rasterize_noalloc")
+
+
+# ---------------------------------------------------------------------------
+# batched path
+# ---------------------------------------------------------------------------
+
+def mer_batch_plan(items, tile: int) -> MerBatchTotals:
+    """items: ctypes array of MerItem (host); fills the offsets in place and returns the totals."""
+    tot = MerBatchTotals()
+    _check(lib().mer_batch_plan(ctypes.cast(items, ctypes.c_void_p), len(items), tile, ctypes.byref(tot)),
+           "mer_batch_plan")
+    return tot
+
+
+def mer_batch_workspace_size(tot: MerBatchTotals, bin_capacity: int = 0) -> int:
+    return int(lib().mer_batch_workspace_size(ctypes.byref(tot), bin_capacity))
+
+
+def mer_batch_project(verts, cams, items_dev, tot, vpix):
+    _check(lib().mer_batch_project(_ptr(verts), _ptr(cams), _ptr(items_dev), ctypes.byref(tot), _ptr(vpix), _stream()),
+           "mer_batch_project")
+
+
+def mer_batch_rasterize(vpix, tris, items_dev, tot, workspace, index, depth=None, bary=None, persistent_ctas=0):
+    _check(lib().mer_batch_rasterize(_ptr(vpix), _ptr(tris), _ptr(items_dev), ctypes.byref(tot), _ptr(workspace),
+                                     workspace.numel() * workspace.element_size(), _ptr(index), _ptr(depth),
+                                     _ptr(bary), persistent_ctas, _stream()), "mer_batch_rasterize")
+
+
+def mer_batch_shade(vpix, tris, items_dev, tot, index, attr, tex, bg, sh: MerShading, image, status_ws=None):
+    bgc = (ctypes.c_float * max(1, sh.C))(*[float(x) for x in bg])
+    _check(lib().mer_batch_shade(_ptr(vpix), _ptr(tris), _ptr(items_dev), ctypes.byref(tot), _ptr(index), _ptr(attr),
+                                 _ptr(tex), ctypes.cast(bgc, ctypes.c_void_p), ctypes.byref(sh), _ptr(image),
+                                 _ptr(status_ws), _stream()), "mer_batch_shade")
+
+
+def mer_batch_backward(vpix, tris, items_dev, tot, index, image, grad_image, attr, tex, sh: MerShading, terms: int,
+                       grad_vpix, grad_attr, workspace, persistent_ctas=0):
+    _check(lib().mer_batch_backward(_ptr(vpix), _ptr(tris), _ptr(items_dev), ctypes.byref(tot), _ptr(index),
+                                    _ptr(image), _ptr(grad_image), _ptr(attr), _ptr(tex), ctypes.byref(sh), terms,
+                                    _ptr(grad_vpix), _ptr(grad_attr), _ptr(workspace), persistent_ctas, _stream()),
+           "mer_batch_backward")
+
+
+def mer_batch_project_backward(cams, items_dev, tot, vpix, grad_vpix, grad_verts):
+    _check(lib().mer_batch_project_backward(_ptr(cams), _ptr(items_dev), ctypes.byref(tot), _ptr(vpix),
+                                            _ptr(grad_vpix), _ptr(grad_verts), _stream()),
+           "mer_batch_project_backward")

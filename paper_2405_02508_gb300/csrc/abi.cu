@@ -19,6 +19,20 @@ extern "C" int mer_launch_backward(const mer_vertex*, int, const int*, int, int,
                                    const float*, const float*, const float*, const mer_shading*, int, double*, float*,
                                    void*, cudaStream_t);
 
+extern "C" size_t mer_batch_raster_workspace_size(long long, long long, long long);
+extern "C" int mer_launch_batch_rasterize(const mer_vertex*, const int*, const mer_item*, int, long long, long long, int,
+                                          void*, size_t, int*, float*, float*, int, cudaStream_t);
+extern "C" int mer_launch_project_batch(const float*, const mer_camera*, const mer_item*, int, long long, mer_vertex*,
+                                        cudaStream_t);
+extern "C" int mer_launch_project_backward_batch(const mer_camera*, const mer_item*, int, long long, const mer_vertex*,
+                                                 const double*, float*, cudaStream_t);
+extern "C" int mer_launch_shade_batch(const mer_vertex*, const int*, const mer_item*, int, long long, const int*,
+                                      const float*, const float*, const float*, const mer_shading*, float*, void*,
+                                      cudaStream_t);
+extern "C" int mer_launch_backward_batch(const mer_vertex*, const int*, const mer_item*, int, long long, const int*,
+                                         const float*, const float*, const float*, const float*, const mer_shading*,
+                                         int, double*, float*, void*, int, cudaStream_t);
+
 namespace {
 
 inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
@@ -147,6 +161,106 @@ int mer_project_backward(int V, const mer_camera* cams, int n, const mer_vertex*
     if ((long long)V * n == 0) return MER_OK;
     if (!cams || !vpix || !grad_vpix || !grad_verts) return MER_EINVAL;
     return mer_launch_project_backward(V, cams, n, vpix, grad_vpix, grad_verts, S(stream));
+}
+
+// ---- batched path ----
+
+int mer_batch_plan(mer_item* items, int n_items, int tile, mer_batch_totals* totals) {
+    if (!totals || n_items < 0 || (n_items > 0 && !items)) return MER_EINVAL;
+    if (tile != 16 && tile != 32 && tile != 64) return MER_EINVAL;
+    int64_t vrec = 0, trec = 0, pix = 0, tiles = 0, btiles = 0;
+    for (int i = 0; i < n_items; ++i) {
+        mer_item& m = items[i];
+        if (m.V < 0 || m.T < 0 || m.H < 0 || m.W < 0 || m.H > mer::kMaxDim || m.W > mer::kMaxDim || m.cam < 0 ||
+            m.vert < 0 || m.tri < 0)
+            return MER_EINVAL;
+        m.vrec = vrec;
+        m.trec = trec;
+        m.pix = pix;
+        m.tile = tiles;
+        m.btile = btiles;
+        vrec += m.V;
+        trec += m.T;
+        pix += (int64_t)m.H * m.W;
+        tiles += (int64_t)((m.W + tile - 1) / tile) * ((m.H + tile - 1) / tile);
+        btiles += (int64_t)((m.W + 31) / 32) * ((m.H + 7) / 8);
+    }
+    const int64_t lim = (int64_t)1 << 31;
+    if (vrec >= lim || trec >= lim || pix >= lim || tiles >= lim || btiles >= lim) return MER_EINVAL;
+    totals->vrecs = vrec;
+    totals->trecs = trec;
+    totals->pixels = pix;
+    totals->tiles = tiles;
+    totals->btiles = btiles;
+    totals->n_items = n_items;
+    totals->tile = tile;
+    return MER_OK;
+}
+
+size_t mer_batch_workspace_size(const mer_batch_totals* t, int64_t bin_capacity) {
+    if (!t) return 0;
+    return mer_batch_raster_workspace_size(t->tiles, t->trecs, (long long)bin_capacity);
+}
+
+static bool totals_ok(const mer_batch_totals* t, const mer_item* items) {
+    return t && t->n_items >= 0 && (t->n_items == 0 || items) && t->vrecs >= 0 && t->trecs >= 0 && t->pixels >= 0;
+}
+
+int mer_batch_project(const float* verts, const mer_camera* cams, const mer_item* items, const mer_batch_totals* t,
+                      mer_vertex* vpix, void* stream) {
+    if (!totals_ok(t, items)) return MER_EINVAL;
+    if (t->vrecs == 0) return MER_OK;
+    if (!verts || !cams || !vpix) return MER_EINVAL;
+    return mer_launch_project_batch(verts, cams, items, t->n_items, t->vrecs, vpix, S(stream));
+}
+
+int mer_batch_rasterize(const mer_vertex* vpix, const int32_t* tris, const mer_item* items, const mer_batch_totals* t,
+                        void* workspace, size_t workspace_bytes, int32_t* index, float* depth, float* bary,
+                        int persistent_ctas, void* stream) {
+    if (!totals_ok(t, items) || (t->tile != 16 && t->tile != 32 && t->tile != 64)) return MER_EINVAL;
+    if (t->pixels == 0) return MER_OK;
+    if (!workspace || !aligned256(workspace) || !index || persistent_ctas < 0) return MER_EINVAL;
+    if (t->trecs > 0 && (!tris || !vpix)) return MER_EINVAL;
+    if (workspace_bytes < mer_batch_raster_workspace_size(t->tiles, t->trecs, 1)) return MER_EINVAL;
+    return mer_launch_batch_rasterize(vpix, tris, items, t->n_items, t->trecs, t->tiles, t->tile, workspace,
+                                      workspace_bytes, index, depth, bary, persistent_ctas, S(stream));
+}
+
+int mer_batch_shade(const mer_vertex* vpix, const int32_t* tris, const mer_item* items, const mer_batch_totals* t,
+                    const int32_t* index, const float* attr, const float* tex, const float* bg_host,
+                    const mer_shading* sh, float* image, void* status_ws, void* stream) {
+    if (!totals_ok(t, items) || !shading_ok(sh)) return MER_EINVAL;
+    if (t->pixels == 0) return MER_OK;
+    if (!index || !image || (t->trecs > 0 && (!tris || !vpix))) return MER_EINVAL;
+    if (sh->n_main > 0 && !attr) return MER_EINVAL;
+    if (sh->uv_offset >= 0 && !tex) return MER_EINVAL;
+    if (status_ws && !aligned256(status_ws)) return MER_EINVAL;
+    return mer_launch_shade_batch(vpix, tris, items, t->n_items, t->pixels, index, attr, tex, bg_host, sh, image,
+                                  status_ws, S(stream));
+}
+
+int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_item* items, const mer_batch_totals* t,
+                       const int32_t* index, const float* image, const float* grad_image, const float* attr,
+                       const float* tex, const mer_shading* sh, int terms, double* grad_vpix, float* grad_attr,
+                       void* workspace, int persistent_ctas, void* stream) {
+    if (!totals_ok(t, items) || !shading_ok(sh)) return MER_EINVAL;
+    if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT)) return MER_EINVAL;
+    if (t->pixels == 0 || terms == 0) return MER_OK;
+    if (!index || !grad_image || (t->vrecs > 0 && !grad_vpix) || (t->trecs > 0 && (!tris || !vpix))) return MER_EINVAL;
+    if ((terms & MER_EDGE) && !image) return MER_EINVAL;
+    if ((terms & MER_INTERIOR) && sh->n_main > 0 && !attr) return MER_EINVAL;
+    if ((terms & MER_INTERIOR) && sh->uv_offset >= 0 && !tex) return MER_EINVAL;
+    if (!workspace || !aligned256(workspace) || persistent_ctas < 0) return MER_EINVAL;
+    return mer_launch_backward_batch(vpix, tris, items, t->n_items, t->btiles, index, image, grad_image, attr, tex, sh,
+                                     terms, grad_vpix, grad_attr, workspace, persistent_ctas, S(stream));
+}
+
+int mer_batch_project_backward(const mer_camera* cams, const mer_item* items, const mer_batch_totals* t,
+                               const mer_vertex* vpix, const double* grad_vpix, float* grad_verts, void* stream) {
+    if (!totals_ok(t, items)) return MER_EINVAL;
+    if (t->vrecs == 0) return MER_OK;
+    if (!cams || !vpix || !grad_vpix || !grad_verts) return MER_EINVAL;
+    return mer_launch_project_backward_batch(cams, items, t->n_items, t->vrecs, vpix, grad_vpix, grad_verts, S(stream));
 }
 
 int mer_sync_status(void* workspace, int64_t* total_bins, void* stream) {

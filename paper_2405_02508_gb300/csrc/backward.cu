@@ -73,50 +73,63 @@ __device__ __forceinline__ int table_slot(int* keys, int vid) {
     return -1;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
-                                                       const int* __restrict__ index, const float* __restrict__ image,
-                                                       const float* __restrict__ grad, const float* __restrict__ attr,
-                                                       const float* __restrict__ tex, BwdArgs a,
-                                                       double* __restrict__ grad_vpix, float* __restrict__ grad_attr,
-                                                       void* ws) {
-    __shared__ int sidx[kHH][kHW];
-    __shared__ int skey[kSlots];
-    __shared__ float sval[kSlots][3];
-    const int tiles_per_view = a.ntx * a.nty;
-    const int view = blockIdx.x / tiles_per_view;
-    const int local = blockIdx.x % tiles_per_view;
-    const int tx = local % a.ntx, ty = local / a.ntx;
-    const size_t plane = (size_t)a.H * a.W;
-    const int* idx_v = index + (size_t)view * plane;
+// One item of a backward pass: a mesh seen by one camera, bases of all its arrays.
+struct BItem {
+    const mer_vertex* vb;   // vertex records
+    const int* tris;        // triangles (item-local vertex ids)
+    const int* index;       // index image [H, W]
+    const float* image;     // shaded image [H, W, C]
+    const float* grad;      // dL/d image [H, W, C]
+    const float* attr;      // attributes [V, C_attr]
+    double* gv;             // grad_vpix [V, 3]
+    float* gattr;           // grad_attr [V, C_attr] or null
+    int V, T, H, W;
+};
+
+struct BwdShared {
+    int sidx[kHH][kHW];
+    int skey[kSlots];
+    float sval[kSlots][3];
+};
+
+// The 32x8 tile (tx, ty) of an item.  All threads of the CTA call it together; it ends with a barrier so
+// the shared buffers can be reused for the next tile.
+__device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, const BwdArgs& a,
+                                              const float* __restrict__ tex, BwdShared& S, void* ws) {
     for (int i = threadIdx.x; i < kSlots; i += kThreads) {
-        skey[i] = -1;
-        sval[i][0] = 0.f;
-        sval[i][1] = 0.f;
-        sval[i][2] = 0.f;
+        S.skey[i] = -1;
+        S.sval[i][0] = 0.f;
+        S.sval[i][1] = 0.f;
+        S.sval[i][2] = 0.f;
     }
     for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
         const int hy = i / kHW, hx = i % kHW;
         const int gx = tx * kTW + hx - 1, gy = ty * kTH + hy - 1;
-        sidx[hy][hx] = (gx >= 0 && gx < a.W && gy >= 0 && gy < a.H) ? __ldg(idx_v + (size_t)gy * a.W + gx) : -2;
+        S.sidx[hy][hx] = (gx >= 0 && gx < it.W && gy >= 0 && gy < it.H) ? __ldg(it.index + (size_t)gy * it.W + gx) : -2;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
     const int x = tx * kTW + lane, y = ty * kTH + row;
     const int C = a.sh.C;
-    const mer_vertex* vb = vpix + (size_t)view * a.V;
-    int t = (x < a.W && y < a.H) ? sidx[row + 1][lane + 1] : -1;
+    const mer_vertex* vb = it.vb;
+    const int* tris = it.tris;
+    const float* grad = it.grad;
+    const float* image = it.image;
+    const float* attr = it.attr;
+    float* grad_attr = it.gattr;
+    int t = (x < it.W && y < it.H) ? S.sidx[row + 1][lane + 1] : -1;
     int vid[3] = {0, 0, 0};
     float c0[3] = {0.f, 0.f, 0.f}, c1[3] = {0.f, 0.f, 0.f}, c2[3] = {0.f, 0.f, 0.f};  // per vertex: x, y, zeta
-    if (t >= a.T) {
+    if (t >= it.T) {
         set_status(ws, kStatusRange);
         t = -1;
     }
-    if (t >= 0 && !tri_ids(tris, t, a.V, vid)) {
+    if (t >= 0 && !tri_ids(tris, t, it.V, vid)) {
         set_status(ws, kStatusRange);
         t = -1;
     }
     if (t >= 0) {
-        const size_t p = (size_t)view * plane + (size_t)y * a.W + x;
+        const size_t p = (size_t)y * it.W + x;
         const float* gp = grad + p * C;
         const VRec rv[3] = {load_vrec(vb + vid[0]), load_vrec(vb + vid[1]), load_vrec(vb + vid[2])};
         const Bary B = screen_bary(rv, x, y);
@@ -208,14 +221,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __re
             for (int d = 0; d < 4; ++d) {
                 const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
                 const int ddy = d == 2 ? -1 : (d == 3 ? 1 : 0);
-                const int tq = sidx[row + 1 + ddy][lane + 1 + ddx];
+                const int tq = S.sidx[row + 1 + ddy][lane + 1 + ddx];
                 if (tq == t || tq == -2) continue;
                 const int qx = x + ddx, qy = y + ddy;
                 const int axis = ddx != 0 ? 0 : 1;
                 bool inter = false;
                 int vq[3] = {0, 0, 0};
                 if (tq >= 0) {
-                    if (tq >= a.T || !tri_ids(tris, tq, a.V, vq)) {
+                    if (tq >= it.T || !tri_ids(tris, tq, it.V, vq)) {
                         set_status(ws, kStatusRange);
                         continue;
                     }
@@ -235,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __re
                     }
                 }
                 // Eq. 11 with A = left/top pixel, B = right/bottom pixel
-                const size_t q = (size_t)view * plane + (size_t)qy * a.W + qx;
+                const size_t q = (size_t)qy * it.W + qx;
                 const float* gq = grad + q * C;
                 const float* iq = image + q * C;
                 const bool p_is_a = ddx > 0 || ddy > 0;
@@ -305,15 +318,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __re
     }
     const int tnext = __shfl_down_sync(full, t, 1);
     const bool tail = lane == 31 || tnext != t;
-    double* gvv = grad_vpix + (size_t)view * a.V * 3;
+    double* gvv = it.gv;
     if (tail && t >= 0 && any) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const int sl = table_slot(skey, vid[k]);
+            const int sl = table_slot(S.skey, vid[k]);
             if (sl >= 0) {
-                atomicAdd(&sval[sl][0], c0[k]);
-                atomicAdd(&sval[sl][1], c1[k]);
-                atomicAdd(&sval[sl][2], c2[k]);
+                atomicAdd(&S.sval[sl][0], c0[k]);
+                atomicAdd(&S.sval[sl][1], c1[k]);
+                atomicAdd(&S.sval[sl][2], c2[k]);
             } else {  // table full: straight to global memory
                 atomicAdd(gvv + 3 * (size_t)vid[k], (double)c0[k]);
                 atomicAdd(gvv + 3 * (size_t)vid[k] + 1, (double)c1[k]);
@@ -323,18 +336,107 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __re
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kSlots; i += kThreads) {
-        const int v = skey[i];
+        const int v = S.skey[i];
         if (v < 0) continue;
-        const float s0 = sval[i][0], s1 = sval[i][1], s2 = sval[i][2];
+        const float s0 = S.sval[i][0], s1 = S.sval[i][1], s2 = S.sval[i][2];
         if (s0 != 0.f) atomicAdd(gvv + 3 * (size_t)v, (double)s0);
         if (s1 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 1, (double)s1);
         if (s2 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 2, (double)s2);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
+                                                       const int* __restrict__ index, const float* __restrict__ image,
+                                                       const float* __restrict__ grad, const float* __restrict__ attr,
+                                                       const float* __restrict__ tex, BwdArgs a,
+                                                       double* __restrict__ grad_vpix, float* __restrict__ grad_attr,
+                                                       void* ws) {
+    __shared__ BwdShared S;
+    const int tiles_per_view = a.ntx * a.nty;
+    const int view = blockIdx.x / tiles_per_view;
+    const int local = blockIdx.x % tiles_per_view;
+    const size_t plane = (size_t)a.H * a.W;
+    BItem it;
+    it.vb = vpix + (size_t)view * a.V;
+    it.tris = tris;
+    it.index = index + (size_t)view * plane;
+    it.image = image ? image + (size_t)view * plane * a.sh.C : nullptr;
+    it.grad = grad + (size_t)view * plane * a.sh.C;
+    it.attr = attr;
+    it.gv = grad_vpix + (size_t)view * a.V * 3;
+    it.gattr = grad_attr;
+    it.V = a.V; it.T = a.T; it.H = a.H; it.W = a.W;
+    backward_tile(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
+}
+
+// Persistent: each CTA takes the next backward tile of any item from the work queue.
+__global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex* __restrict__ vpix,
+                                                             const int* __restrict__ tris,
+                                                             const mer_item* __restrict__ items, int n_items,
+                                                             long long btiles, const int* __restrict__ index,
+                                                             const float* __restrict__ image,
+                                                             const float* __restrict__ grad,
+                                                             const float* __restrict__ attr,
+                                                             const float* __restrict__ tex, BwdArgs a,
+                                                             double* __restrict__ grad_vpix,
+                                                             float* __restrict__ grad_attr, void* ws) {
+    __shared__ BwdShared S;
+    __shared__ long long s_tile;
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    const int C = a.sh.C, Ca = a.sh.C_attr;
+    while (true) {
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_backward, 1ull);
+        __syncthreads();
+        const long long g = s_tile;
+        if (g >= btiles) break;
+        const mer_item m = items[find_item(items, n_items, g, kFieldBtile)];
+        const int ntx = (m.W + kTW - 1) / kTW;
+        const int local = (int)(g - m.btile);
+        BItem it;
+        it.vb = vpix + m.vrec;
+        it.tris = tris + 3 * m.tri;
+        it.index = index + m.pix;
+        it.image = image ? image + (size_t)m.pix * C : nullptr;
+        it.grad = grad + (size_t)m.pix * C;
+        it.attr = attr ? attr + (size_t)m.vert * Ca : nullptr;
+        it.gv = grad_vpix + 3 * (size_t)m.vrec;
+        it.gattr = grad_attr ? grad_attr + (size_t)m.vert * Ca : nullptr;
+        it.V = m.V; it.T = m.T; it.H = m.H; it.W = m.W;
+        backward_tile(it, local % ntx, local / ntx, a, tex, S, ws);  // ends with a barrier
     }
 }
 
 }  // namespace mer
 
 using namespace mer;
+
+extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
+                                         long long btiles, const int* index, const float* image,
+                                         const float* grad_image, const float* attr, const float* tex,
+                                         const mer_shading* sh, int terms, double* grad_vpix, float* grad_attr,
+                                         void* ws, int persistent_ctas, cudaStream_t s) {
+    if (btiles == 0) return 0;
+    BwdArgs a;
+    a.sh = *sh;
+    a.terms = terms;
+    a.n = 0; a.H = 0; a.W = 0; a.V = 0; a.T = 0; a.ntx = 0; a.nty = 0;
+    a.tex_stride = sh->tex_c > 0 ? sh->tex_c : sh->n_main;
+    a.tex_vec4 = a.tex_stride == 4 && tex && (reinterpret_cast<uintptr_t>(tex) & 15u) == 0;
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    if (cudaMemsetAsync(&hdr->queue_backward, 0, sizeof(unsigned long long), s) != cudaSuccess) return 2;
+    unsigned grid = persistent_ctas > 0 ? (unsigned)persistent_ctas : 0u;
+    if (grid == 0) {
+        int per_sm = 0, sms = 0, dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 2;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 2;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_batch, kThreads, 0) != cudaSuccess) return 2;
+        grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
+    }
+    k_backward_batch<<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, image, grad_image, attr, tex,
+                                               a, grad_vpix, grad_attr, ws);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
 
 extern "C" int mer_launch_backward(const mer_vertex* vpix, int V, const int* tris, int T, int n, int H, int W,
                                    const int* index, const float* image, const float* grad_image, const float* attr,

@@ -22,7 +22,9 @@ struct WsHeader {
     int pad0;
     long long total_bins;
     long long capacity;
-    int pad[58];
+    unsigned long long queue_raster;    // work-queue counters of the persistent kernels
+    unsigned long long queue_backward;
+    int pad[54];
 };
 static_assert(sizeof(WsHeader) == 256, "header");
 constexpr int kStatusOverflow = 1;
@@ -413,6 +415,29 @@ __device__ __forceinline__ void tex_grad_uv(const float* __restrict__ tex, int T
     }
     gu = (float)TW * su;
     gv = t.clamped ? 0.0f : (float)TH * sv;
+}
+
+// Item of a batch that holds global element g of one offset field (largest i with key(i) <= g; items
+// with an empty range share their key with the next item and are never returned for a valid g).
+enum ItemField { kFieldVrec = 0, kFieldTrec, kFieldPix, kFieldTile, kFieldBtile };
+
+__device__ __forceinline__ long long item_key(const mer_item& it, int f) {
+    switch (f) {
+        case kFieldVrec: return it.vrec;
+        case kFieldTrec: return it.trec;
+        case kFieldPix: return it.pix;
+        case kFieldTile: return it.tile;
+        default: return it.btile;
+    }
+}
+
+__device__ __forceinline__ int find_item(const mer_item* __restrict__ items, int n, long long g, int f) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_key(items[mid], f) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 __device__ __forceinline__ void set_status(void* ws, int bit) {

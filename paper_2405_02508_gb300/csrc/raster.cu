@@ -1,14 +1,16 @@
 // raster.cu -- rasterization module with z-buffer (Supp. B): triangle setup and
 // tile binning, then a per-tile raster that stages the tile's triangle records in
-// shared memory and keeps each pixel's nearest fragment in registers.
+// shared memory and resolves visibility in a shared-memory z-buffer.
 //
-// Pipeline per call (all views of one mesh at once):
-//   k_setup_count : per (view, triangle): cull, exact setup record, pixel bbox,
+// Pipeline per call:
+//   setup + count : per (item, triangle): cull, exact setup record, pixel bbox,
 //                   count the bin tiles it overlaps
-//   k_scan_*      : exclusive scan of the per-tile counts -> list offsets
-//   k_bin_fill    : scatter triangle ids into the per-tile lists
-//   k_raster<TS>  : one CTA per (view, tile): coverage + depth test, write
-//                   index / depth / bary
+//   scan          : exclusive scan of the per-tile counts -> list offsets
+//   fill          : scatter triangle ids into the per-tile lists
+//   raster<TS>    : one CTA per tile: coverage + depth test, write index / depth / bary
+// The per-item bodies are shared by the multi-view entry point (items = the views of
+// one mesh, addressed by strides) and by the batched path (items from a table; the
+// raster runs as a persistent kernel pulling tiles from a device work queue).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -17,9 +19,15 @@
 
 namespace mer {
 
-struct BinGeom {
-    int n, H, W, T, V, tile, ntx, nty;
-    long long tiles_per_view;
+// One item of a raster pass: a mesh seen by one camera.
+struct RItem {
+    const mer_vertex* vpix;  // the item's vertex records
+    const int* tris;         // the item's triangles (item-local vertex ids)
+    TriRaster* recs;         // the item's raster records
+    int V, T, H, W;
+    int ntx, nty;            // bin tiles across / down
+    long long tile0;         // first global bin tile of the item
+    long long pix0;          // first global pixel of the item
 };
 
 __device__ __forceinline__ int floordiv256(int a) { return a >> 8; }  // arithmetic shift = floor
@@ -33,11 +41,9 @@ __device__ __forceinline__ void centre_range(int mn, int mx, int lim, int& lo, i
     hi = min(hi, lim - 1);
 }
 
-__global__ void k_setup_count(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris, BinGeom g,
-                              TriRaster* __restrict__ recs, int* __restrict__ counts, void* ws) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)g.T * g.n) return;
-    const int view = (int)(i / g.T), t = (int)(i % g.T);
+// Setup record of triangle t of an item; counts the bin tiles it overlaps.
+__device__ __forceinline__ void setup_count_one(const RItem& it, int t, int tile, int* __restrict__ counts,
+                                                void* ws) {
     TriRaster r;
     r.flags = (int)0x80000000;  // culled unless set up below
     r.bx0 = 1; r.bx1 = 0; r.by0 = 1; r.by1 = 0;
@@ -45,32 +51,31 @@ __global__ void k_setup_count(const mer_vertex* __restrict__ vpix, const int* __
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        vid[k] = tris[3 * (size_t)t + k];
-        if (vid[k] < 0 || vid[k] >= g.V) ok = false;
+        vid[k] = it.tris[3 * (size_t)t + k];
+        if (vid[k] < 0 || vid[k] >= it.V) ok = false;
     }
     if (!ok) {
         set_status(ws, kStatusRange);
-        recs[i] = r;
+        it.recs[t] = r;
         return;
     }
-    const mer_vertex* vb = vpix + (size_t)view * g.V;
     mer_vertex v[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        v[k] = vb[vid[k]];
+        v[k] = it.vpix[vid[k]];
         if ((v[k].flags & kValid) != kValid) ok = false;
         r.X[k] = v[k].X;
         r.Y[k] = v[k].Y;
     }
-    if (!ok) { recs[i] = r; return; }
+    if (!ok) { it.recs[t] = r; return; }
     const int64_t a2 = (int64_t)(r.X[1] - r.X[0]) * (r.Y[2] - r.Y[0]) - (int64_t)(r.Y[1] - r.Y[0]) * (r.X[2] - r.X[0]);
-    if (a2 == 0) { recs[i] = r; return; }
+    if (a2 == 0) { it.recs[t] = r; return; }
     const int mnx = min(r.X[0], min(r.X[1], r.X[2])), mxx = max(r.X[0], max(r.X[1], r.X[2]));
     const int mny = min(r.Y[0], min(r.Y[1], r.Y[2])), mxy = max(r.Y[0], max(r.Y[1], r.Y[2]));
     int x0, x1, y0, y1;
-    centre_range(mnx, mxx, g.W, x0, x1);
-    centre_range(mny, mxy, g.H, y0, y1);
-    if (x0 > x1 || y0 > y1) { recs[i] = r; return; }
+    centre_range(mnx, mxx, it.W, x0, x1);
+    centre_range(mny, mxy, it.H, y0, y1);
+    if (x0 > x1 || y0 > y1) { it.recs[t] = r; return; }
     const int s = a2 > 0 ? 1 : -1;
     int fl = a2 > 0 ? 0 : 8;
 #pragma unroll
@@ -86,10 +91,22 @@ __global__ void k_setup_count(const mer_vertex* __restrict__ vpix, const int* __
 #pragma unroll
     for (int k = 0; k < 3; ++k) r.zd[k] = __fdiv_rn(v[k].zeta, Df);
     r.bx0 = (short)x0; r.bx1 = (short)x1; r.by0 = (short)y0; r.by1 = (short)y1;
-    recs[i] = r;
-    int* cnt = counts + (size_t)view * g.tiles_per_view;
-    for (int ty = y0 / g.tile; ty <= y1 / g.tile; ++ty)
-        for (int tx = x0 / g.tile; tx <= x1 / g.tile; ++tx) atomicAdd(cnt + ty * g.ntx + tx, 1);
+    it.recs[t] = r;
+    int* cnt = counts + it.tile0;
+    for (int ty = y0 / tile; ty <= y1 / tile; ++ty)
+        for (int tx = x0 / tile; tx <= x1 / tile; ++tx) atomicAdd(cnt + ty * it.ntx + tx, 1);
+}
+
+__device__ __forceinline__ void fill_one(const RItem& it, int t, int tile, const int* __restrict__ offs,
+                                         int* __restrict__ cursor, int* __restrict__ list, long long capacity) {
+    const TriRaster& r = it.recs[t];
+    if (r.flags < 0) return;
+    for (int ty = r.by0 / tile; ty <= r.by1 / tile; ++ty)
+        for (int tx = r.bx0 / tile; tx <= r.bx1 / tile; ++tx) {
+            const size_t g = it.tile0 + (size_t)ty * it.ntx + tx;
+            const long long pos = (long long)offs[g] + atomicAdd(cursor + g, 1);
+            if (pos < capacity) list[pos] = t;
+        }
 }
 
 // --- exclusive scan of the tile counts (3 kernels, 1024 elements per block) ---
@@ -147,6 +164,7 @@ __global__ void k_scan_sums(int* __restrict__ sums, int nb, void* ws, long long 
         WsHeader* h = reinterpret_cast<WsHeader*>(ws);
         h->total_bins = carry;
         h->capacity = capacity;
+        h->queue_raster = 0ull;
         if (carry > capacity) atomicOr(&h->status, kStatusOverflow);
     }
 }
@@ -159,24 +177,8 @@ __global__ void k_scan_add(int* __restrict__ out, long long N, const int* __rest
     }
 }
 
-__global__ void k_bin_fill(const TriRaster* __restrict__ recs, BinGeom g, const int* __restrict__ offs,
-                           int* __restrict__ cursor, int* __restrict__ list, long long capacity) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)g.T * g.n) return;
-    const TriRaster& r = recs[i];
-    if (r.flags < 0) return;
-    const int view = (int)(i / g.T), t = (int)(i % g.T);
-    const size_t base = (size_t)view * g.tiles_per_view;
-    for (int ty = r.by0 / g.tile; ty <= r.by1 / g.tile; ++ty)
-        for (int tx = r.bx0 / g.tile; tx <= r.bx1 / g.tile; ++tx) {
-            const size_t tile = base + (size_t)ty * g.ntx + tx;
-            const long long pos = (long long)offs[tile] + atomicAdd(cursor + tile, 1);
-            if (pos < capacity) list[pos] = t;
-        }
-}
-
 // --- raster ---
-// One CTA per (view, tile).  The tile's triangle records are staged in shared memory; each warp takes one
+// One CTA per tile.  The tile's triangle records are staged in shared memory; each warp takes one
 // triangle at a time and its lanes test the pixels of the triangle's bounding box inside the tile (32 at a
 // time), so the work follows the bounding-box areas and every lane of a warp runs the same triangle.  The
 // nearest fragment per pixel is resolved in a shared-memory z-buffer by a 64-bit atomicMax on
@@ -185,26 +187,23 @@ constexpr int kStage = 256;  // triangle records staged per round
 constexpr int kRasterThreads = 256;
 
 template <int TS>
-__global__ void __launch_bounds__(kRasterThreads) k_raster(const TriRaster* __restrict__ recs, BinGeom g,
-                                                           const int* __restrict__ offs, const int* __restrict__ cnts,
-                                                           const int* __restrict__ list, const mer_vertex* __restrict__ vpix,
-                                                           const int* __restrict__ tris, void* ws, long long capacity,
-                                                           int* __restrict__ index, float* __restrict__ depth,
-                                                           float* __restrict__ bary) {
-    __shared__ TriRaster sh[kStage];
-    __shared__ int sh_id[kStage];
-    __shared__ unsigned long long zbuf[TS * TS];
-    const WsHeader* hdr = reinterpret_cast<const WsHeader*>(ws);
-    const bool overflow = hdr->total_bins > capacity;
-    const long long tile = blockIdx.x;
-    const int view = (int)(tile / g.tiles_per_view);
-    const int local = (int)(tile % g.tiles_per_view);
-    const int ty = local / g.ntx, tx = local % g.ntx;
+struct RasterShared {
+    TriRaster rec[kStage];
+    int id[kStage];
+    unsigned long long zbuf[TS * TS];
+};
+
+template <int TS>
+__device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, const int* __restrict__ offs,
+                                            const int* __restrict__ cnts, const int* __restrict__ list,
+                                            bool overflow, RasterShared<TS>& S, int* __restrict__ index,
+                                            float* __restrict__ depth, float* __restrict__ bary) {
+    const long long tile = it.tile0 + local_tile;
+    const int ty = local_tile / it.ntx, tx = local_tile % it.ntx;
     const int ox = tx * TS, oy = ty * TS;
-    for (int i = threadIdx.x; i < TS * TS; i += kRasterThreads) zbuf[i] = 0ull;
+    for (int i = threadIdx.x; i < TS * TS; i += kRasterThreads) S.zbuf[i] = 0ull;
     const int count = overflow ? 0 : cnts[tile];
     const int off = overflow ? 0 : offs[tile];
-    const TriRaster* rv = recs + (size_t)view * g.T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = kRasterThreads / 32;
     for (int base = 0; base < count; base += kStage) {
@@ -212,18 +211,18 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(const TriRaster* __re
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += kRasterThreads) {
             const int t = list[off + base + j];
-            sh[j] = rv[t];
-            sh_id[j] = t;
+            S.rec[j] = it.recs[t];
+            S.id[j] = t;
         }
         __syncthreads();
         for (int j = warp; j < m; j += kWarps) {
-            const TriRaster& r = sh[j];
+            const TriRaster& r = S.rec[j];
             const int x0 = max((int)r.bx0, ox), x1 = min((int)r.bx1, ox + TS - 1);
             const int y0 = max((int)r.by0, oy), y1 = min((int)r.by1, oy + TS - 1);
             const int bw = x1 - x0 + 1, bh = y1 - y0 + 1;
             if (bw <= 0 || bh <= 0) continue;
             const int npx = bw * bh;
-            const unsigned idkey = 0xFFFFFFFFu - (unsigned)sh_id[j];
+            const unsigned idkey = 0xFFFFFFFFu - (unsigned)S.id[j];
             // lane -> (dx, dy) in the bbox, then advance by 32 pixels per pass without dividing per pixel
             int dy = lane / bw;
             int dx = lane - dy * bw;
@@ -247,24 +246,23 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(const TriRaster* __re
                     z = depth_key(r, E);
                 }
                 const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | idkey;
-                atomicMax(&zbuf[(py - oy) * TS + (px - ox)], key);
+                atomicMax(&S.zbuf[(py - oy) * TS + (px - ox)], key);
             }
         }
     }
     __syncthreads();
-    const mer_vertex* vb = vpix + (size_t)view * g.V;
     for (int i = threadIdx.x; i < TS * TS; i += kRasterThreads) {
         const int px = ox + (i % TS), py = oy + (i / TS);
-        if (px >= g.W || py >= g.H) continue;
-        const unsigned long long key = zbuf[i];
+        if (px >= it.W || py >= it.H) continue;
+        const unsigned long long key = S.zbuf[i];
         const int t = key ? (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull)) : -1;
-        const size_t p = ((size_t)view * g.H + py) * g.W + px;
+        const size_t p = (size_t)it.pix0 + (size_t)py * it.W + px;
         index[p] = t;
         if (!depth && !bary) continue;
         float Z = 0.f, b1 = 0.f, b2 = 0.f;
         if (t >= 0) {
-            const VRec v[3] = {load_vrec(vb + tris[3 * (size_t)t]), load_vrec(vb + tris[3 * (size_t)t + 1]),
-                               load_vrec(vb + tris[3 * (size_t)t + 2])};
+            const VRec v[3] = {load_vrec(it.vpix + it.tris[3 * (size_t)t]), load_vrec(it.vpix + it.tris[3 * (size_t)t + 1]),
+                               load_vrec(it.vpix + it.tris[3 * (size_t)t + 2])};
             const Bary B = screen_bary(v, px, py);
             const float z0 = v[0].zeta, z1 = v[1].zeta, z2 = v[2].zeta;
             const float s = B.lam[0] * z0 + B.lam[1] * z1 + B.lam[2] * z2;
@@ -279,6 +277,125 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(const TriRaster* __re
             bary[2 * p + 1] = b2;
         }
     }
+    __syncthreads();  // the next tile reuses the shared buffers
+}
+
+// ---- multi-view entry: items are the views of one mesh, addressed by strides ----
+struct BinGeom {
+    int n, H, W, T, V, tile, ntx, nty;
+    long long tiles_per_view;
+};
+
+__device__ __forceinline__ RItem view_item(const BinGeom& g, const mer_vertex* vpix, const int* tris,
+                                           TriRaster* recs, int view) {
+    RItem it;
+    it.vpix = vpix + (size_t)view * g.V;
+    it.tris = tris;
+    it.recs = recs + (size_t)view * g.T;
+    it.V = g.V; it.T = g.T; it.H = g.H; it.W = g.W;
+    it.ntx = g.ntx; it.nty = g.nty;
+    it.tile0 = (long long)view * g.tiles_per_view;
+    it.pix0 = (long long)view * g.H * g.W;
+    return it;
+}
+
+__global__ void k_setup_count(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris, BinGeom g,
+                              TriRaster* __restrict__ recs, int* __restrict__ counts, void* ws) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)g.T * g.n) return;
+    const int view = (int)(i / g.T), t = (int)(i % g.T);
+    setup_count_one(view_item(g, vpix, tris, recs, view), t, g.tile, counts, ws);
+}
+
+__global__ void k_bin_fill(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris, BinGeom g,
+                           TriRaster* __restrict__ recs, const int* __restrict__ offs, int* __restrict__ cursor,
+                           int* __restrict__ list, long long capacity) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)g.T * g.n) return;
+    const int view = (int)(i / g.T), t = (int)(i % g.T);
+    fill_one(view_item(g, vpix, tris, recs, view), t, g.tile, offs, cursor, list, capacity);
+}
+
+template <int TS>
+__global__ void __launch_bounds__(kRasterThreads) k_raster(TriRaster* __restrict__ recs, BinGeom g,
+                                                           const int* __restrict__ offs, const int* __restrict__ cnts,
+                                                           const int* __restrict__ list, const mer_vertex* __restrict__ vpix,
+                                                           const int* __restrict__ tris, void* ws, long long capacity,
+                                                           int* __restrict__ index, float* __restrict__ depth,
+                                                           float* __restrict__ bary) {
+    __shared__ RasterShared<TS> S;
+    const WsHeader* hdr = reinterpret_cast<const WsHeader*>(ws);
+    const bool overflow = hdr->total_bins > capacity;
+    const long long tile = blockIdx.x;
+    const int view = (int)(tile / g.tiles_per_view);
+    const int local = (int)(tile % g.tiles_per_view);
+    raster_tile<TS>(view_item(g, vpix, tris, recs, view), local, offs, cnts, list, overflow, S, index, depth, bary);
+}
+
+// ---- batched entry: items from a table ----
+struct BatchGeom {
+    const mer_item* items;
+    int n_items, tile;
+    long long trecs, tiles;
+};
+
+__device__ __forceinline__ RItem batch_item(const mer_item& m, int tile, const mer_vertex* vpix, const int* tris,
+                                            TriRaster* recs) {
+    RItem it;
+    it.vpix = vpix + m.vrec;
+    it.tris = tris + 3 * m.tri;
+    it.recs = recs + m.trec;
+    it.V = m.V; it.T = m.T; it.H = m.H; it.W = m.W;
+    it.ntx = (m.W + tile - 1) / tile;
+    it.nty = (m.H + tile - 1) / tile;
+    it.tile0 = m.tile;
+    it.pix0 = m.pix;
+    return it;
+}
+
+__global__ void k_setup_count_batch(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris, BatchGeom b,
+                                    TriRaster* __restrict__ recs, int* __restrict__ counts, void* ws) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.trecs) return;
+    const int k = find_item(b.items, b.n_items, i, kFieldTrec);
+    const mer_item m = b.items[k];
+    setup_count_one(batch_item(m, b.tile, vpix, tris, recs), (int)(i - m.trec), b.tile, counts, ws);
+}
+
+__global__ void k_bin_fill_batch(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris, BatchGeom b,
+                                 TriRaster* __restrict__ recs, const int* __restrict__ offs,
+                                 int* __restrict__ cursor, int* __restrict__ list, long long capacity) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.trecs) return;
+    const int k = find_item(b.items, b.n_items, i, kFieldTrec);
+    const mer_item m = b.items[k];
+    fill_one(batch_item(m, b.tile, vpix, tris, recs), (int)(i - m.trec), b.tile, offs, cursor, list, capacity);
+}
+
+// Persistent: each CTA takes the next global tile from the work queue until none is left.
+template <int TS>
+__global__ void __launch_bounds__(kRasterThreads) k_raster_batch(TriRaster* __restrict__ recs, BatchGeom b,
+                                                                 const int* __restrict__ offs,
+                                                                 const int* __restrict__ cnts,
+                                                                 const int* __restrict__ list,
+                                                                 const mer_vertex* __restrict__ vpix,
+                                                                 const int* __restrict__ tris, void* ws,
+                                                                 long long capacity, int* __restrict__ index,
+                                                                 float* __restrict__ depth, float* __restrict__ bary) {
+    __shared__ RasterShared<TS> S;
+    __shared__ long long s_tile;
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    const bool overflow = hdr->total_bins > capacity;
+    while (true) {
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_raster, 1ull);
+        __syncthreads();
+        const long long g = s_tile;
+        if (g >= b.tiles) break;
+        const int k = find_item(b.items, b.n_items, g, kFieldTile);
+        const mer_item m = b.items[k];
+        raster_tile<TS>(batch_item(m, b.tile, vpix, tris, recs), (int)(g - m.tile), offs, cnts, list, overflow, S,
+                        index, depth, bary);  // ends with a barrier: s_tile may be overwritten after it
+    }
 }
 
 }  // namespace mer
@@ -287,32 +404,49 @@ using namespace mer;
 
 namespace {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-}
 
 struct RasterLayout {
     size_t hdr, counts, offs, cursor, sums, recs, list, total;
     long long ntiles, nblocks, capacity;
 };
 
-static RasterLayout raster_layout(int V, int T, int n, int H, int W, int tile, long long capacity) {
-    (void)V;
+RasterLayout layout_for(long long ntiles, long long nrecs, long long capacity) {
     RasterLayout L;
-    const long long ntx = (W + tile - 1) / tile, nty = (H + tile - 1) / tile;
-    L.ntiles = ntx * nty * (long long)n;
-    L.nblocks = (L.ntiles + kScanBlock - 1) / kScanBlock;
-    if (capacity <= 0) capacity = 4LL * n * T + 2LL * L.ntiles + 1024;
+    L.ntiles = ntiles;
+    L.nblocks = (ntiles + kScanBlock - 1) / kScanBlock;
+    if (capacity <= 0) capacity = 4LL * nrecs + 2LL * ntiles + 1024;
     L.capacity = capacity;
     size_t o = 0;
     L.hdr = o; o += align256(sizeof(WsHeader));
-    L.counts = o; o += align256((size_t)L.ntiles * 4);
-    L.offs = o; o += align256((size_t)L.ntiles * 4);
-    L.cursor = o; o += align256((size_t)L.ntiles * 4);
+    L.counts = o; o += align256((size_t)ntiles * 4);
+    L.offs = o; o += align256((size_t)ntiles * 4);
+    L.cursor = o; o += align256((size_t)ntiles * 4);
     L.sums = o; o += align256((size_t)(L.nblocks + 1) * 4);
-    L.recs = o; o += align256((size_t)n * T * sizeof(TriRaster));
+    L.recs = o; o += align256((size_t)nrecs * sizeof(TriRaster));
     L.list = o; o += align256((size_t)capacity * 4);
     L.total = o;
     return L;
 }
+
+RasterLayout raster_layout(int V, int T, int n, int H, int W, int tile, long long capacity) {
+    (void)V;
+    const long long ntx = (W + tile - 1) / tile, nty = (H + tile - 1) / tile;
+    return layout_for(ntx * nty * (long long)n, (long long)n * T, capacity);
+}
+
+// Scan of the per-tile counts and the header totals.
+int launch_scan(const RasterLayout& L, char* base, long long capacity, cudaStream_t s) {
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
+    int* counts = reinterpret_cast<int*>(base + L.counts);
+    int* offs = reinterpret_cast<int*>(base + L.offs);
+    int* cursor = reinterpret_cast<int*>(base + L.cursor);
+    int* sums = reinterpret_cast<int*>(base + L.sums);
+    if (L.nblocks > 0) k_scan_blocks<<<(unsigned)L.nblocks, kScanBlock, 0, s>>>(counts, L.ntiles, offs, sums);
+    k_scan_sums<<<1, kScanBlock, 0, s>>>(sums, (int)L.nblocks, hdr, capacity);
+    if (L.nblocks > 0) k_scan_add<<<(unsigned)L.nblocks, kScanBlock, 0, s>>>(offs, L.ntiles, sums, cursor);
+    return 0;
+}
+}  // namespace
 
 extern "C" size_t mer_raster_workspace_size(int V, int T, int n, int H, int W, int tile, long long capacity) {
     return raster_layout(V, T, n, H, W, tile, capacity).total;
@@ -331,7 +465,6 @@ extern "C" int mer_launch_rasterize(const mer_vertex* vpix, int V, const int* tr
     int* counts = reinterpret_cast<int*>(base + L.counts);
     int* offs = reinterpret_cast<int*>(base + L.offs);
     int* cursor = reinterpret_cast<int*>(base + L.cursor);
-    int* sums = reinterpret_cast<int*>(base + L.sums);
     TriRaster* recs = reinterpret_cast<TriRaster*>(base + L.recs);
     int* list = reinterpret_cast<int*>(base + L.list);
     BinGeom g;
@@ -342,21 +475,74 @@ extern "C" int mer_launch_rasterize(const mer_vertex* vpix, int V, const int* tr
     // header: the status word is sticky until mer_sync_status; k_scan_sums writes the totals
     if (cudaMemsetAsync(counts, 0, (size_t)L.ntiles * 4, s) != cudaSuccess) return 2;
     const long long NT = (long long)T * n;
-    if (NT > 0) {
-        k_setup_count<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(vpix, tris, g, recs, counts, hdr);
-    }
-    k_scan_blocks<<<(unsigned)L.nblocks, kScanBlock, 0, s>>>(counts, L.ntiles, offs, sums);
-    k_scan_sums<<<1, kScanBlock, 0, s>>>(sums, (int)L.nblocks, hdr, capacity);
-    k_scan_add<<<(unsigned)L.nblocks, kScanBlock, 0, s>>>(offs, L.ntiles, sums, cursor);
-    if (NT > 0) {
-        k_bin_fill<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(recs, g, offs, cursor, list, capacity);
-    }
+    if (NT > 0) k_setup_count<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(vpix, tris, g, recs, counts, hdr);
+    launch_scan(L, base, capacity, s);
+    if (NT > 0)
+        k_bin_fill<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(vpix, tris, g, recs, offs, cursor, list, capacity);
     const unsigned grid = (unsigned)L.ntiles;
     switch (tile) {
         case 8: k_raster<8><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
         case 16: k_raster<16><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
         case 32: k_raster<32><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
         default: return 1;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+extern "C" size_t mer_batch_raster_workspace_size(long long tiles, long long trecs, long long capacity) {
+    return layout_for(tiles, trecs, capacity).total;
+}
+
+template <int TS>
+static int launch_raster_batch(unsigned grid, TriRaster* recs, BatchGeom b, const int* offs, const int* counts,
+                               const int* list, const mer_vertex* vpix, const int* tris, void* hdr, long long capacity,
+                               int* index, float* depth, float* bary, cudaStream_t s) {
+    if (grid == 0) {
+        int per_sm = 0, sms = 0, dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 2;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 2;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_batch<TS>, kRasterThreads, 0) != cudaSuccess)
+            return 2;
+        grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
+    }
+    k_raster_batch<TS><<<grid, kRasterThreads, 0, s>>>(recs, b, offs, counts, list, vpix, tris, hdr, capacity, index,
+                                                       depth, bary);
+    return 0;
+}
+
+extern "C" int mer_launch_batch_rasterize(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
+                                          long long trecs, long long tiles, int tile, void* ws, size_t ws_bytes,
+                                          int* index, float* depth, float* bary, int persistent_ctas,
+                                          cudaStream_t s) {
+    RasterLayout L = layout_for(tiles, trecs, 1);
+    if (ws_bytes < L.total) return 1;
+    const long long capacity = (long long)((ws_bytes - L.list) / 4);
+    L = layout_for(tiles, trecs, capacity);
+    char* base = static_cast<char*>(ws);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
+    int* counts = reinterpret_cast<int*>(base + L.counts);
+    int* offs = reinterpret_cast<int*>(base + L.offs);
+    int* cursor = reinterpret_cast<int*>(base + L.cursor);
+    TriRaster* recs = reinterpret_cast<TriRaster*>(base + L.recs);
+    int* list = reinterpret_cast<int*>(base + L.list);
+    BatchGeom b;
+    b.items = items; b.n_items = n_items; b.tile = tile; b.trecs = trecs; b.tiles = tiles;
+    if (tiles > 0 && cudaMemsetAsync(counts, 0, (size_t)tiles * 4, s) != cudaSuccess) return 2;
+    if (trecs > 0) k_setup_count_batch<<<(unsigned)((trecs + 255) / 256), 256, 0, s>>>(vpix, tris, b, recs, counts, hdr);
+    launch_scan(L, base, capacity, s);  // also resets the raster work queue
+    if (trecs > 0)
+        k_bin_fill_batch<<<(unsigned)((trecs + 255) / 256), 256, 0, s>>>(vpix, tris, b, recs, offs, cursor, list,
+                                                                        capacity);
+    if (tiles > 0) {
+        const unsigned grid = persistent_ctas > 0 ? (unsigned)persistent_ctas : 0u;
+        int rc = 1;
+        switch (tile) {
+            case 16: rc = launch_raster_batch<16>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, s); break;
+            case 32: rc = launch_raster_batch<32>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, s); break;
+            case 64: rc = launch_raster_batch<64>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, s); break;
+            default: return 1;
+        }
+        if (rc) return rc;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

@@ -19,12 +19,11 @@ struct ShadeArgs {
     bool tex_vec4;   // stride 4 and 16-byte aligned: 128-bit texel loads
 };
 
-__global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* __restrict__ tris, int T, int n, int H,
-                        int W, const int* __restrict__ index, const float* __restrict__ attr,
-                        const float* __restrict__ tex, ShadeArgs a, float* __restrict__ image, void* ws) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long npix = (long long)n * H * W;
-    if (p >= npix) return;
+// Pixel (x, y) of an item: vb / tris / attr are the item's bases, p the global pixel.
+__device__ __forceinline__ void shade_pixel(const mer_vertex* __restrict__ vb, int V, const int* __restrict__ tris,
+                                            int T, int x, int y, size_t p, const int* __restrict__ index,
+                                            const float* __restrict__ attr, const float* __restrict__ tex,
+                                            const ShadeArgs& a, float* __restrict__ image, void* ws) {
     const int C = a.sh.C;
     float* o = image + (size_t)p * C;
     const int t = index[p];
@@ -46,10 +45,6 @@ __global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* _
             if (c < C) o[c] = a.bg[c];
         return;
     }
-    const int view = (int)(p / ((long long)H * W));
-    const int rem = (int)(p % ((long long)H * W));
-    const int y = rem / W, x = rem % W;
-    const mer_vertex* vb = vpix + (size_t)view * V;
     const VRec v[3] = {load_vrec(vb + i0), load_vrec(vb + i1), load_vrec(vb + i2)};
     const int vid[3] = {i0, i1, i2};
     const Bary B = screen_bary(v, x, y);
@@ -92,20 +87,58 @@ __global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* _
     if (a.sh.depth_ch >= 0) o[a.sh.depth_ch] = is;
 }
 
+__global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* __restrict__ tris, int T, int n, int H,
+                        int W, const int* __restrict__ index, const float* __restrict__ attr,
+                        const float* __restrict__ tex, ShadeArgs a, float* __restrict__ image, void* ws) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long npix = (long long)n * H * W;
+    if (p >= npix) return;
+    const int view = (int)(p / ((long long)H * W));
+    const int rem = (int)(p % ((long long)H * W));
+    shade_pixel(vpix + (size_t)view * V, V, tris, T, rem % W, rem / W, (size_t)p, index, attr, tex, a, image, ws);
+}
+
+__global__ void k_shade_batch(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
+                              const mer_item* __restrict__ items, int n_items, long long pixels,
+                              const int* __restrict__ index, const float* __restrict__ attr,
+                              const float* __restrict__ tex, ShadeArgs a, float* __restrict__ image, void* ws) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= pixels) return;
+    const mer_item m = items[find_item(items, n_items, p, kFieldPix)];
+    const int rem = (int)(p - m.pix);
+    shade_pixel(vpix + m.vrec, m.V, tris + 3 * m.tri, m.T, rem % m.W, rem / m.W, (size_t)p, index,
+                attr ? attr + (size_t)m.vert * a.sh.C_attr : nullptr, tex, a, image, ws);
+}
+
 }  // namespace mer
 
 using namespace mer;
+
+static ShadeArgs make_shade_args(const float* tex, const float* bg, const mer_shading* sh) {
+    ShadeArgs a;
+    a.sh = *sh;
+    for (int c = 0; c < kMaxC; ++c) a.bg[c] = (bg && c < sh->C) ? bg[c] : 0.f;
+    a.tex_stride = sh->tex_c > 0 ? sh->tex_c : sh->n_main;
+    a.tex_vec4 = a.tex_stride == 4 && tex && (reinterpret_cast<uintptr_t>(tex) & 15u) == 0;
+    return a;
+}
+
+extern "C" int mer_launch_shade_batch(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
+                                      long long pixels, const int* index, const float* attr, const float* tex,
+                                      const float* bg, const mer_shading* sh, float* image, void* ws, cudaStream_t s) {
+    if (pixels == 0) return 0;
+    const ShadeArgs a = make_shade_args(tex, bg, sh);
+    k_shade_batch<<<(unsigned)((pixels + 255) / 256), 256, 0, s>>>(vpix, tris, items, n_items, pixels, index, attr,
+                                                                   tex, a, image, ws);
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
 
 extern "C" int mer_launch_shade(const mer_vertex* vpix, int V, const int* tris, int T, int n, int H, int W,
                                 const int* index, const float* attr, const float* tex, const float* bg,
                                 const mer_shading* sh, float* image, void* ws, cudaStream_t s) {
     const long long npix = (long long)n * H * W;
     if (npix == 0) return 0;
-    ShadeArgs a;
-    a.sh = *sh;
-    for (int c = 0; c < kMaxC; ++c) a.bg[c] = (bg && c < sh->C) ? bg[c] : 0.f;
-    a.tex_stride = sh->tex_c > 0 ? sh->tex_c : sh->n_main;
-    a.tex_vec4 = a.tex_stride == 4 && tex && (reinterpret_cast<uintptr_t>(tex) & 15u) == 0;
+    const ShadeArgs a = make_shade_args(tex, bg, sh);
     k_shade<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(vpix, V, tris, T, n, H, W, index, attr, tex, a, image, ws);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

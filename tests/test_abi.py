@@ -51,3 +51,26 @@ def test_host_only_calls():
     assert lib.mer_rasterize(None, 3, None, 1, 1, 16, 16, 16, None, 0, None, None, None, None) == binding.MER_EINVAL
     assert lib.mer_project(None, 3, None, 1, None, None) == binding.MER_EINVAL
     assert lib.mer_project(None, 0, None, 1, None, None) == binding.MER_OK  # empty: nothing to do
+
+
+def test_batch_plan_offsets():
+    """mer_batch_plan (host only): running offsets per item and totals; oversized items are refused."""
+    from paper_2405_02508_gb300 import binding
+
+    arr = (binding.MerItem * 3)()
+    sizes = [(10, 7, 40, 50), (0, 0, 0, 0), (5, 3, 17, 33)]
+    for k, (V, T, H, W) in enumerate(sizes):
+        arr[k].V, arr[k].T, arr[k].H, arr[k].W = V, T, H, W
+    tot = binding.mer_batch_plan(arr, 32)
+    assert [arr[k].vrec for k in range(3)] == [0, 10, 10]
+    assert [arr[k].trec for k in range(3)] == [0, 7, 7]
+    assert [arr[k].pix for k in range(3)] == [0, 2000, 2000]
+    assert [arr[k].tile for k in range(3)] == [0, 4, 4]  # ceil(50/32) * ceil(40/32) = 4
+    assert [arr[k].btile for k in range(3)] == [0, 10, 10]  # ceil(50/32) * ceil(40/8) = 10
+    assert (tot.vrecs, tot.trecs, tot.pixels, tot.tiles, tot.btiles) == (15, 10, 2000 + 561, 4 + 2, 10 + 6)
+    assert binding.mer_batch_workspace_size(tot) > 0
+    arr[0].H = 9000
+    import pytest
+
+    with pytest.raises(binding.MerError):
+        binding.mer_batch_plan(arr, 32)
