@@ -177,7 +177,8 @@ int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, 
  * grad_vpix [n,V,3] float64 (+=): dL/d(x_s, y_s, zeta) per view.  The per-pixel
  * arithmetic is FP32; the sums over pixels are accumulated in FP64 because a
  * vertex gradient component can be a strongly cancelling sum of many terms.
- * grad_attr [V,C_attr] (+=) or NULL: dL/d(attr) of the interior term. */
+ * grad_attr [V,C_attr] (+=) or NULL: dL/d(attr) of the interior term (interpolation mode: at most 4
+ * interpolated channels; texture mode: the u, v columns). */
 int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
                  const int32_t* index, const float* image, const float* grad_image,
                  const float* attr, const float* tex, const mer_shading* shading_host, int terms,

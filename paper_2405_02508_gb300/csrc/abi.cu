@@ -134,6 +134,7 @@ int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int 
     if ((terms & MER_EDGE) && !image) return MER_EINVAL;
     if ((terms & MER_INTERIOR) && sh->n_main > 0 && !attr) return MER_EINVAL;
     if ((terms & MER_INTERIOR) && sh->uv_offset >= 0 && !tex) return MER_EINVAL;
+    if (grad_attr && sh->uv_offset < 0 && sh->n_main > 4) return MER_EINVAL;  // attribute gradients: <= 4 channels
     if (status_ws && !aligned256(status_ws)) return MER_EINVAL;
     return mer_launch_backward(vpix, V, tris, T, n, H, W, index, image, grad_image, attr, tex, sh, terms, grad_vpix,
                                grad_attr, status_ws, S(stream));
@@ -250,6 +251,7 @@ int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_it
     if ((terms & MER_EDGE) && !image) return MER_EINVAL;
     if ((terms & MER_INTERIOR) && sh->n_main > 0 && !attr) return MER_EINVAL;
     if ((terms & MER_INTERIOR) && sh->uv_offset >= 0 && !tex) return MER_EINVAL;
+    if (grad_attr && sh->uv_offset < 0 && sh->n_main > 4) return MER_EINVAL;  // attribute gradients: <= 4 channels
     if (!workspace || !aligned256(workspace) || persistent_ctas < 0) return MER_EINVAL;
     return mer_launch_backward_batch(vpix, tris, items, t->n_items, t->btiles, index, image, grad_image, attr, tex, sh,
                                      terms, grad_vpix, grad_attr, workspace, persistent_ctas, S(stream));

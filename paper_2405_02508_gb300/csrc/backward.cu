@@ -86,14 +86,20 @@ struct BItem {
     int V, T, H, W;
 };
 
+constexpr int kMaxA = 4;  // attribute-gradient channels carried through the per-tile aggregation
+
 struct BwdShared {
     int sidx[kHH][kHW];
     int skey[kSlots];
     float sval[kSlots][3];
+    float sattr[kSlots][kMaxA];
 };
 
 // The 32x8 tile (tx, ty) of an item.  All threads of the CTA call it together; it ends with a barrier so
 // the shared buffers can be reused for the next tile.
+// ATTR: also produce the attribute gradients (channels [a0, a0 + A) of each vertex's attribute row, A <= 4:
+// the interpolated channels, or (u, v) in texture mode), aggregated like the vertex gradients.
+template <bool ATTR>
 __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, const BwdArgs& a,
                                               const float* __restrict__ tex, BwdShared& S, void* ws) {
     for (int i = threadIdx.x; i < kSlots; i += kThreads) {
@@ -101,7 +107,13 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
         S.sval[i][0] = 0.f;
         S.sval[i][1] = 0.f;
         S.sval[i][2] = 0.f;
+        if (ATTR) {
+#pragma unroll
+            for (int j = 0; j < kMaxA; ++j) S.sattr[i][j] = 0.f;
+        }
     }
+    const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
+    const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
     for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
         const int hy = i / kHW, hx = i % kHW;
         const int gx = tx * kTW + hx - 1, gy = ty * kTH + hy - 1;
@@ -120,6 +132,11 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
     int t = (x < it.W && y < it.H) ? S.sidx[row + 1][lane + 1] : -1;
     int vid[3] = {0, 0, 0};
     float c0[3] = {0.f, 0.f, 0.f}, c1[3] = {0.f, 0.f, 0.f}, c2[3] = {0.f, 0.f, 0.f};  // per vertex: x, y, zeta
+    float ca[3][kMaxA];  // per vertex: attribute-gradient channels (ATTR)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < kMaxA; ++j) ca[k][j] = 0.f;
     if (t >= it.T) {
         set_status(ws, kStatusRange);
         t = -1;
@@ -156,10 +173,14 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
                     D01 += gc * (a0 - a1);
                     D02 += gc * (a0 - a2);
                     D12 += gc * (a1 - a2);
-                    if (grad_attr) {
-                        atomicAdd(grad_attr + (size_t)vid[0] * Ca + c, b[0] * gc);
-                        atomicAdd(grad_attr + (size_t)vid[1] * Ca + c, b[1] * gc);
-                        atomicAdd(grad_attr + (size_t)vid[2] * Ca + c, b[2] * gc);
+                    if (ATTR) {
+#pragma unroll
+                        for (int j = 0; j < kMaxA; ++j)
+                            if (j == c) {
+                                ca[0][j] = b[0] * gc;
+                                ca[1][j] = b[1] * gc;
+                                ca[2][j] = b[2] * gc;
+                            }
                     }
                 }
             } else {
@@ -177,11 +198,11 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
                 D01 = gu * (uk[0] - uk[1]) + gv * (vk[0] - vk[1]);
                 D02 = gu * (uk[0] - uk[2]) + gv * (vk[0] - vk[2]);
                 D12 = gu * (uk[1] - uk[2]) + gv * (vk[1] - vk[2]);
-                if (grad_attr) {
+                if (ATTR) {
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        atomicAdd(grad_attr + (size_t)vid[k] * Ca + a.sh.uv_offset, b[k] * gu);
-                        atomicAdd(grad_attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1, b[k] * gv);
+                        ca[k][0] = b[k] * gu;
+                        ca[k][1] = b[k] * gv;
                     }
                 }
             }
@@ -291,7 +312,7 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
     const bool head = lane == 0 || tprev != t;
     const unsigned heads = __ballot_sync(full, head);
     const int seg = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of this run
-    const bool contributes = t >= 0 && (c0[0] != 0.f || c1[0] != 0.f || c2[0] != 0.f || c0[1] != 0.f ||
+    const bool contributes = t >= 0 && (ATTR || c0[0] != 0.f || c1[0] != 0.f || c2[0] != 0.f || c0[1] != 0.f ||
                                         c1[1] != 0.f || c2[1] != 0.f || c0[2] != 0.f || c1[2] != 0.f ||
                                         c2[2] != 0.f);
     const unsigned any = __ballot_sync(full, contributes);
@@ -306,13 +327,21 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
         const bool take = lane - dlt >= seg;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float a0 = __shfl_up_sync(full, c0[k], dlt);
-            const float a1 = __shfl_up_sync(full, c1[k], dlt);
-            const float a2 = __shfl_up_sync(full, c2[k], dlt);
+            const float a0_ = __shfl_up_sync(full, c0[k], dlt);
+            const float a1_ = __shfl_up_sync(full, c1[k], dlt);
+            const float a2_ = __shfl_up_sync(full, c2[k], dlt);
             if (take) {
-                c0[k] += a0;
-                c1[k] += a1;
-                c2[k] += a2;
+                c0[k] += a0_;
+                c1[k] += a1_;
+                c2[k] += a2_;
+            }
+            if (ATTR) {
+#pragma unroll
+                for (int j = 0; j < kMaxA; ++j) {
+                    if (j >= A) break;
+                    const float aj = __shfl_up_sync(full, ca[k][j], dlt);
+                    if (take) ca[k][j] += aj;
+                }
             }
         }
     }
@@ -327,10 +356,20 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
                 atomicAdd(&S.sval[sl][0], c0[k]);
                 atomicAdd(&S.sval[sl][1], c1[k]);
                 atomicAdd(&S.sval[sl][2], c2[k]);
+                if (ATTR) {
+#pragma unroll
+                    for (int j = 0; j < kMaxA; ++j)
+                        if (j < A) atomicAdd(&S.sattr[sl][j], ca[k][j]);
+                }
             } else {  // table full: straight to global memory
                 atomicAdd(gvv + 3 * (size_t)vid[k], (double)c0[k]);
                 atomicAdd(gvv + 3 * (size_t)vid[k] + 1, (double)c1[k]);
                 atomicAdd(gvv + 3 * (size_t)vid[k] + 2, (double)c2[k]);
+                if (ATTR) {
+#pragma unroll
+                    for (int j = 0; j < kMaxA; ++j)
+                        if (j < A) atomicAdd(grad_attr + (size_t)vid[k] * a.sh.C_attr + a0 + j, ca[k][j]);
+                }
             }
         }
     }
@@ -342,10 +381,19 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
         if (s0 != 0.f) atomicAdd(gvv + 3 * (size_t)v, (double)s0);
         if (s1 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 1, (double)s1);
         if (s2 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 2, (double)s2);
+        if (ATTR) {
+#pragma unroll
+            for (int j = 0; j < kMaxA; ++j) {
+                if (j >= A) break;
+                const float sa = S.sattr[i][j];
+                if (sa != 0.f) atomicAdd(grad_attr + (size_t)v * a.sh.C_attr + a0 + j, sa);
+            }
+        }
     }
     __syncthreads();
 }
 
+template <bool ATTR>
 __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
                                                        const int* __restrict__ index, const float* __restrict__ image,
                                                        const float* __restrict__ grad, const float* __restrict__ attr,
@@ -367,10 +415,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __re
     it.gv = grad_vpix + (size_t)view * a.V * 3;
     it.gattr = grad_attr;
     it.V = a.V; it.T = a.T; it.H = a.H; it.W = a.W;
-    backward_tile(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
+    backward_tile<ATTR>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
 }
 
 // Persistent: each CTA takes the next backward tile of any item from the work queue.
+template <bool ATTR>
 __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex* __restrict__ vpix,
                                                              const int* __restrict__ tris,
                                                              const mer_item* __restrict__ items, int n_items,
@@ -403,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex
         it.gv = grad_vpix + 3 * (size_t)m.vrec;
         it.gattr = grad_attr ? grad_attr + (size_t)m.vert * Ca : nullptr;
         it.V = m.V; it.T = m.T; it.H = m.H; it.W = m.W;
-        backward_tile(it, local % ntx, local / ntx, a, tex, S, ws);  // ends with a barrier
+        backward_tile<ATTR>(it, local % ntx, local / ntx, a, tex, S, ws);  // ends with a barrier
     }
 }
 
@@ -430,11 +479,18 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
         int per_sm = 0, sms = 0, dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 2;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 2;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_batch, kThreads, 0) != cudaSuccess) return 2;
+        const cudaError_t e = grad_attr
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_batch<true>, kThreads, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_batch<false>, kThreads, 0);
+        if (e != cudaSuccess) return 2;
         grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
     }
-    k_backward_batch<<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, image, grad_image, attr, tex,
-                                               a, grad_vpix, grad_attr, ws);
+    if (grad_attr)
+        k_backward_batch<true><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, image, grad_image,
+                                                         attr, tex, a, grad_vpix, grad_attr, ws);
+    else
+        k_backward_batch<false><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, image, grad_image,
+                                                          attr, tex, a, grad_vpix, grad_attr, ws);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -452,7 +508,11 @@ extern "C" int mer_launch_backward(const mer_vertex* vpix, int V, const int* tri
     a.tex_vec4 = a.tex_stride == 4 && tex && (reinterpret_cast<uintptr_t>(tex) & 15u) == 0;
     const long long blocks = (long long)a.ntx * a.nty * n;
     if (blocks == 0) return 0;
-    k_backward<<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, image, grad_image, attr, tex, a, grad_vpix,
-                                                    grad_attr, ws);
+    if (grad_attr)
+        k_backward<true><<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, image, grad_image, attr, tex, a,
+                                                               grad_vpix, grad_attr, ws);
+    else
+        k_backward<false><<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, image, grad_image, attr, tex, a,
+                                                                grad_vpix, grad_attr, ws);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

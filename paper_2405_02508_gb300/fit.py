@@ -1,0 +1,84 @@
+"""Inverse rendering over an uneven batch of meshes: fit perturbed vertex positions to images rendered from
+the unperturbed meshes (mask + normal L2), with Adam.
+
+``BatchRender`` is the autograd function of the batched path: forward renders every item, backward runs
+the micro-edge + interior kernels and returns d(loss)/d(vertices) and d(loss)/d(attributes).  Vertex
+normals (the attributes) are recomputed from the current positions with PyTorch each step, so the
+attribute gradient reaches the positions through PyTorch's own autograd.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from .batch import BatchRenderer
+
+
+class BatchRender(torch.autograd.Function):
+    """image [pixels, C] = render(verts, attr).  The renderer keeps the forward image for the backward, so
+    call backward before the next forward on the same renderer."""
+
+    @staticmethod
+    def forward(ctx, verts, attr, br: BatchRenderer):
+        br.forward(verts.contiguous(), attr.contiguous())
+        ctx.br = br
+        ctx.save_for_backward(attr)
+        return br.image.clone()
+
+    @staticmethod
+    def backward(ctx, grad_image):
+        (attr,) = ctx.saved_tensors
+        br = ctx.br
+        ga = torch.zeros_like(attr) if ctx.needs_input_grad[1] else None
+        gv = br.backward(grad_image.contiguous(), attr, None, grad_attr=ga)
+        return gv.clone(), ga, None
+
+
+def vertex_normals(verts: torch.Tensor, tris: torch.Tensor) -> torch.Tensor:
+    """Area-weighted, normalised vertex normals (differentiable, PyTorch)."""
+    a, b, c = verts[tris[:, 0]], verts[tris[:, 1]], verts[tris[:, 2]]
+    fn = torch.cross(b - a, c - a, dim=1)
+    vn = torch.zeros_like(verts).index_add_(0, tris[:, 0], fn).index_add_(0, tris[:, 1], fn).index_add_(0, tris[:, 2], fn)
+    return vn / vn.norm(dim=1, keepdim=True).clamp_min(1e-20)
+
+
+class UnevenFit:
+    """The uneven-batch fitting problem on the GPU batched path."""
+
+    def __init__(self, items, sigma: float = 0.01, seed: int = 11, tile: int = 32):
+        self.items = items
+        meshes = [(it.verts, it.tris) for it in items]
+        cams = np.concatenate([it.cams for it in items])
+        self.br = BatchRenderer(meshes, [(k, k, it.H, it.W) for k, it in enumerate(items)], cams,
+                                items[0].shading, 3, None, tile=tile)
+        off = np.cumsum([0] + [len(it.verts) for it in items])
+        self.vert_off = off
+        self.tris_global = torch.from_numpy(np.concatenate([it.tris + off[k] for k, it in enumerate(items)])).long().cuda()
+        self.v_true = torch.from_numpy(np.concatenate([it.verts for it in items])).cuda()
+        rng = np.random.default_rng(seed)
+        self.v_init = self.v_true + torch.from_numpy(rng.normal(0.0, sigma, self.v_true.shape).astype(np.float32)).cuda()
+        with torch.no_grad():
+            self.br.prepare(self.v_true, vertex_normals(self.v_true, self.tris_global))
+            self.target = self.br.image.clone()
+
+    @property
+    def pixels(self) -> int:
+        return int(self.br.tot.pixels)
+
+    def run(self, steps: int, lr: float = 1e-3):
+        verts = self.v_init.clone().requires_grad_(True)
+        opt = torch.optim.Adam([verts], lr=lr)
+        for _ in range(steps):
+            opt.zero_grad(set_to_none=True)
+            img = BatchRender.apply(verts, vertex_normals(verts, self.tris_global), self.br)
+            loss = ((img - self.target) ** 2).sum()
+            loss.backward()
+            opt.step()
+        return verts.detach()
+
+    def rmse(self, verts, subset=None) -> float:
+        d = (verts - self.v_true).double()
+        if subset is not None:
+            rows = np.concatenate([np.arange(self.vert_off[k], self.vert_off[k + 1]) for k in subset])
+            d = d[torch.from_numpy(rows).cuda()]
+        return float(d.pow(2).sum(dim=1).mean().sqrt())

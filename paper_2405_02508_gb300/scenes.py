@@ -349,7 +349,7 @@ def head_multiview(n_views: int = 32, H: int = 2048, W: int = 1334, n: int = 128
 
 
 def uneven_batch(n_items: int = 256, seed: int = 8, res_seed: int = 9,
-                 t_min: float = 500.0, t_max: float = 200000.0):
+                 t_min: float = 500.0, t_max: float = 200000.0, resolutions=(128, 256, 512, 1024)):
     """Uneven batch: ``n_items`` displaced spheres, T log-uniform in [t_min, t_max], res in {128..1024}^2.
 
     Returns a list of Scenes (one camera each); item i is displaced with seed 1000+i.
@@ -358,7 +358,7 @@ def uneven_batch(n_items: int = 256, seed: int = 8, res_seed: int = 9,
     rng = np.random.default_rng(seed)
     T = np.exp(rng.uniform(math.log(t_min), math.log(t_max), n_items))
     rres = np.random.default_rng(res_seed)
-    res = rres.choice([128, 256, 512, 1024], n_items)
+    res = rres.choice(list(resolutions), n_items)
     out = []
     for i in range(n_items):
         ni = max(8, int(round(math.sqrt(T[i] / 8.0))))
