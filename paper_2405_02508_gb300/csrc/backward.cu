@@ -253,12 +253,41 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
                         set_status(ws, kStatusRange);
                         continue;
                     }
-                    int Xq[3], Yq[3];
+                    // Fast exit for triangles sharing an edge (the common case inside a closed mesh): q's
+                    // triangle lies on the side of the shared edge where its third vertex is; p's centre strictly
+                    // on the other side is outside it, so p's fragment gets nothing from this pair.
+                    int nshared = 0, odd = -1, pos_in_t[3];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {  // snapped position only: one 64-bit load per vertex
-                        const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
-                        Xq[k] = xy.x;
-                        Yq[k] = xy.y;
+                    for (int k = 0; k < 3; ++k) {
+                        pos_in_t[k] = vq[k] == vid[0] ? 0 : (vq[k] == vid[1] ? 1 : (vq[k] == vid[2] ? 2 : -1));
+                        if (pos_in_t[k] >= 0) ++nshared; else odd = k;
+                    }
+                    int Xq[3], Yq[3];
+                    if (nshared == 2) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            if (pos_in_t[k] >= 0) {
+                                Xq[k] = X[pos_in_t[k]];
+                                Yq[k] = Y[pos_in_t[k]];
+                            } else {
+                                const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
+                                Xq[k] = xy.x;
+                                Yq[k] = xy.y;
+                            }
+                        }
+                        // shared edge (j, k) opposite vq[odd]: sign of the edge function at the third vertex
+                        // and at p's centre, both exact in 64 bits
+                        const int j = (odd + 1) % 3, k = (odd + 2) % 3;
+                        const int64_t side_d = edge_fn(Xq[j], Yq[j], Xq[k], Yq[k], Xq[odd], Yq[odd]);
+                        const int64_t side_p = edge_fn(Xq[j], Yq[j], Xq[k], Yq[k], 256 * x + 128, 256 * y + 128);
+                        if ((side_d > 0 && side_p < 0) || (side_d < 0 && side_p > 0)) continue;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {  // snapped position only: one 64-bit load per vertex
+                            const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
+                            Xq[k] = xy.x;
+                            Yq[k] = xy.y;
+                        }
                     }
                     // classification (Sec. 4.3): p's fragment scatters only if p's centre lies inside q's
                     // triangle (p on top of it), or both centres lie in each other's triangles (intersection)
