@@ -93,7 +93,138 @@ struct BwdShared {
     int skey[kSlots];
     float sval[kSlots][3];
     float sattr[kSlots][kMaxA];
+    float efrag[kTH][32][3];  // per warp: edge-term fragment gradients returned to the pixel's lane
 };
+
+// Edge term of the warp's row (all 32 lanes call it together).  Lane l owns the fragment of pixel (x0 + l, y)
+// and its triangle t (vertex ids vid, snapped X, Y).  The (pixel, neighbour) pairs whose ids differ are
+// compacted into one list per warp and classified 32 at a time, every lane busy, the source pixel's triangle
+// taken from its lane by shuffle; a pair that scatters to the source fragment adds into that pixel's slot of a
+// per-warp shared buffer, which the owning lane finally adds to (fx, fy, fz).
+__device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, BwdShared& S, void* ws, int row,
+                                          int lane, int x, int y, int t, const int vid[3], const int X[3],
+                                          const int Y[3], float& fx, float& fy, float& fz) {
+    const unsigned full = 0xffffffffu;
+    const int C = a.sh.C;
+    unsigned m[4];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
+        const int ddy = d == 2 ? -1 : (d == 3 ? 1 : 0);
+        const int tq = S.sidx[row + 1 + ddy][lane + 1 + ddx];
+        m[d] = __ballot_sync(full, t >= 0 && tq != t && tq != -2);
+    }
+    const int n0 = __popc(m[0]), n1 = n0 + __popc(m[1]), n2 = n1 + __popc(m[2]), n = n2 + __popc(m[3]);
+    if (n == 0) return;
+    float* acc = &S.efrag[row][0][0];
+    acc[3 * lane] = 0.f;
+    acc[3 * lane + 1] = 0.f;
+    acc[3 * lane + 2] = 0.f;
+    __syncwarp();
+    const int x0 = x - lane;
+    const mer_vertex* vb = it.vb;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const int d = i < n0 ? 0 : (i < n1 ? 1 : (i < n2 ? 2 : 3));
+        const int r = i - (d == 0 ? 0 : (d == 1 ? n0 : (d == 2 ? n1 : n2)));
+        const unsigned md = d == 0 ? m[0] : (d == 1 ? m[1] : (d == 2 ? m[2] : m[3]));
+        const int src = i < n ? (int)__fns(md, 0, r + 1) : lane;
+        const int ts = __shfl_sync(full, t, src);
+        int vs[3], Xs[3], Ys[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            vs[k] = __shfl_sync(full, vid[k], src);
+            Xs[k] = __shfl_sync(full, X[k], src);
+            Ys[k] = __shfl_sync(full, Y[k], src);
+        }
+        if (i >= n) continue;
+        const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
+        const int ddy = d == 2 ? -1 : (d == 3 ? 1 : 0);
+        const int px = x0 + src;
+        const int tq = S.sidx[row + 1 + ddy][src + 1 + ddx];
+        const int qx = px + ddx, qy = y + ddy;
+        const int axis = ddx != 0 ? 0 : 1;
+        bool inter = false;
+        int vq[3] = {0, 0, 0};
+        if (tq >= 0) {
+            if (tq >= it.T || !tri_ids(it.tris, tq, it.V, vq)) {
+                set_status(ws, kStatusRange);
+                continue;
+            }
+            // Fast exit for triangles sharing an edge (the common case inside a closed mesh): q's triangle lies
+            // on the side of the shared edge where its third vertex is; p's centre strictly on the other side
+            // is outside it, so p's fragment gets nothing from this pair.
+            int nshared = 0, odd = -1, pos_in_t[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                pos_in_t[k] = vq[k] == vs[0] ? 0 : (vq[k] == vs[1] ? 1 : (vq[k] == vs[2] ? 2 : -1));
+                if (pos_in_t[k] >= 0) ++nshared; else odd = k;
+            }
+            int Xq[3], Yq[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (nshared == 2 && pos_in_t[k] >= 0) {
+                    Xq[k] = Xs[pos_in_t[k]];
+                    Yq[k] = Ys[pos_in_t[k]];
+                } else {  // snapped position only: one 64-bit load per vertex
+                    const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
+                    Xq[k] = xy.x;
+                    Yq[k] = xy.y;
+                }
+            }
+            if (nshared == 2) {
+                const int j = (odd + 1) % 3, k = (odd + 2) % 3;
+                const int64_t side_d = edge_fn(Xq[j], Yq[j], Xq[k], Yq[k], Xq[odd], Yq[odd]);
+                const int64_t side_p = edge_fn(Xq[j], Yq[j], Xq[k], Yq[k], 256 * px + 128, 256 * y + 128);
+                if ((side_d > 0 && side_p < 0) || (side_d < 0 && side_p > 0)) continue;
+            }
+            // classification (Sec. 4.3): p's fragment scatters only if p's centre lies inside q's triangle
+            // (p on top of it), or both centres lie in each other's triangles (intersection)
+            if (!covers_xy(Xq, Yq, 256 * px + 128, 256 * y + 128)) continue;
+            if (covers_xy(Xs, Ys, 256 * qx + 128, 256 * qy + 128)) {
+                if (!(a.terms & MER_INTERSECT)) continue;
+                inter = true;
+            }
+        }
+        // Eq. 11 with A = left/top pixel, B = right/bottom pixel
+        const size_t p = (size_t)y * it.W + px;
+        const size_t q = (size_t)qy * it.W + qx;
+        const float *gp = it.grad + p * C, *gq = it.grad + q * C, *ip = it.image + p * C, *iq = it.image + q * C;
+        const bool p_is_a = ddx > 0 || ddy > 0;
+        float dLdp = 0.f;
+        for (int c = 0; c < C; ++c) {
+            const float diff = __ldg(ip + c) - __ldg(iq + c);
+            dLdp += 0.5f * (__ldg(gp + c) + __ldg(gq + c)) * (p_is_a ? diff : -diff);
+        }
+        float ex = 0.f, ey = 0.f, ez = 0.f;
+        if (!inter) {
+            if (axis == 0) ex = dLdp; else ey = dLdp;
+        } else {
+            // Eq. 12: p's triangle varies (v), q's triangle is fixed (f), slice (axis, zeta)
+            const VRec rv[3] = {load_vrec(vb + vs[0]), load_vrec(vb + vs[1]), load_vrec(vb + vs[2])};
+            const VRec rq[3] = {load_vrec(vb + vq[0]), load_vrec(vb + vq[1]), load_vrec(vb + vq[2])};
+            float Nv[3], Nf[3];
+            tri_normal(rv, Nv);
+            tri_normal(rq, Nf);
+            const float nv0 = axis == 0 ? Nv[0] : Nv[1], nv1 = Nv[2];
+            const float nf0 = axis == 0 ? Nf[0] : Nf[1], nf1 = Nf[2];
+            const float den = diff_of_products(nf0, nv1, nf1, nv0);
+            const float mag = sqrtf((nv0 * nv0 + nv1 * nv1) * (nf0 * nf0 + nf1 * nf1));
+            if (!(fabsf(den) > 1e-12f * mag)) continue;
+            const float kk = dLdp * (-nf1 / den);
+            if (axis == 0) ex = kk * nv0; else ey = kk * nv0;
+            ez = kk * nv1;
+        }
+        (void)ts;
+        atomicAdd(acc + 3 * src, ex);
+        atomicAdd(acc + 3 * src + 1, ey);
+        atomicAdd(acc + 3 * src + 2, ez);
+    }
+    __syncwarp();
+    fx += acc[3 * lane];
+    fy += acc[3 * lane + 1];
+    fz += acc[3 * lane + 2];
+}
 
 // The 32x8 tile (tx, ty) of an item.  All threads of the CTA call it together; it ends with a barrier so
 // the shared buffers can be reused for the next tile.
@@ -145,13 +276,20 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
         set_status(ws, kStatusRange);
         t = -1;
     }
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    float hz[3] = {0.f, 0.f, 0.f}, lam[3] = {0.f, 0.f, 0.f};
+    int X[3] = {0, 0, 0}, Y[3] = {0, 0, 0};
     if (t >= 0) {
         const size_t p = (size_t)y * it.W + x;
         const float* gp = grad + p * C;
         const VRec rv[3] = {load_vrec(vb + vid[0]), load_vrec(vb + vid[1]), load_vrec(vb + vid[2])};
         const Bary B = screen_bary(rv, x, y);
-        float fx = 0.f, fy = 0.f, fz = 0.f;
-        float hz[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lam[k] = B.lam[k];
+            X[k] = rv[k].X;
+            Y[k] = rv[k].Y;
+        }
 
         if (a.terms & MER_INTERIOR) {
             const float z[3] = {rv[0].zeta, rv[1].zeta, rv[2].zeta};
@@ -230,105 +368,15 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
             fy -= wy;
         }
 
-        if (a.terms & MER_EDGE) {
-            int X[3], Y[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                X[k] = rv[k].X;
-                Y[k] = rv[k].Y;
-            }
-            const float* ip = image + p * C;
-#pragma unroll 1
-            for (int d = 0; d < 4; ++d) {
-                const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
-                const int ddy = d == 2 ? -1 : (d == 3 ? 1 : 0);
-                const int tq = S.sidx[row + 1 + ddy][lane + 1 + ddx];
-                if (tq == t || tq == -2) continue;
-                const int qx = x + ddx, qy = y + ddy;
-                const int axis = ddx != 0 ? 0 : 1;
-                bool inter = false;
-                int vq[3] = {0, 0, 0};
-                if (tq >= 0) {
-                    if (tq >= it.T || !tri_ids(tris, tq, it.V, vq)) {
-                        set_status(ws, kStatusRange);
-                        continue;
-                    }
-                    // Fast exit for triangles sharing an edge (the common case inside a closed mesh): q's
-                    // triangle lies on the side of the shared edge where its third vertex is; p's centre strictly
-                    // on the other side is outside it, so p's fragment gets nothing from this pair.
-                    int nshared = 0, odd = -1, pos_in_t[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        pos_in_t[k] = vq[k] == vid[0] ? 0 : (vq[k] == vid[1] ? 1 : (vq[k] == vid[2] ? 2 : -1));
-                        if (pos_in_t[k] >= 0) ++nshared; else odd = k;
-                    }
-                    int Xq[3], Yq[3];
-                    if (nshared == 2) {
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            if (pos_in_t[k] >= 0) {
-                                Xq[k] = X[pos_in_t[k]];
-                                Yq[k] = Y[pos_in_t[k]];
-                            } else {
-                                const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
-                                Xq[k] = xy.x;
-                                Yq[k] = xy.y;
-                            }
-                        }
-                        // shared edge (j, k) opposite vq[odd]: sign of the edge function at the third vertex
-                        // and at p's centre, both exact in 64 bits
-                        const int j = (odd + 1) % 3, k = (odd + 2) % 3;
-                        const int64_t side_d = edge_fn(Xq[j], Yq[j], Xq[k], Yq[k], Xq[odd], Yq[odd]);
-                        const int64_t side_p = edge_fn(Xq[j], Yq[j], Xq[k], Yq[k], 256 * x + 128, 256 * y + 128);
-                        if ((side_d > 0 && side_p < 0) || (side_d < 0 && side_p > 0)) continue;
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {  // snapped position only: one 64-bit load per vertex
-                            const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
-                            Xq[k] = xy.x;
-                            Yq[k] = xy.y;
-                        }
-                    }
-                    // classification (Sec. 4.3): p's fragment scatters only if p's centre lies inside q's
-                    // triangle (p on top of it), or both centres lie in each other's triangles (intersection)
-                    if (!covers_xy(Xq, Yq, 256 * x + 128, 256 * y + 128)) continue;
-                    if (covers_xy(X, Y, 256 * qx + 128, 256 * qy + 128)) {
-                        if (!(a.terms & MER_INTERSECT)) continue;
-                        inter = true;
-                    }
-                }
-                // Eq. 11 with A = left/top pixel, B = right/bottom pixel
-                const size_t q = (size_t)qy * it.W + qx;
-                const float* gq = grad + q * C;
-                const float* iq = image + q * C;
-                const bool p_is_a = ddx > 0 || ddy > 0;
-                float dLdp = 0.f;
-                for (int c = 0; c < C; ++c) {
-                    const float diff = __ldg(ip + c) - __ldg(iq + c);
-                    dLdp += 0.5f * (__ldg(gp + c) + __ldg(gq + c)) * (p_is_a ? diff : -diff);
-                }
-                if (!inter) {
-                    if (axis == 0) fx += dLdp; else fy += dLdp;
-                    continue;
-                }
-                // Eq. 12: p's triangle varies (v), q's triangle is fixed (f), slice (axis, zeta)
-                const VRec rq[3] = {load_vrec(vb + vq[0]), load_vrec(vb + vq[1]), load_vrec(vb + vq[2])};
-                float Nv[3], Nf[3];
-                tri_normal(rv, Nv);
-                tri_normal(rq, Nf);
-                const float nv0 = axis == 0 ? Nv[0] : Nv[1], nv1 = Nv[2];
-                const float nf0 = axis == 0 ? Nf[0] : Nf[1], nf1 = Nf[2];
-                const float den = diff_of_products(nf0, nv1, nf1, nv0);
-                const float mag = sqrtf((nv0 * nv0 + nv1 * nv1) * (nf0 * nf0 + nf1 * nf1));
-                if (!(fabsf(den) > 1e-12f * mag)) continue;
-                const float kk = dLdp * (-nf1 / den);
-                if (axis == 0) fx += kk * nv0; else fy += kk * nv0;
-                fz += kk * nv1;
-            }
-        }
+    }
+
+    if (a.terms & MER_EDGE) {
+        edge_term(it, a, S, ws, row, lane, x, y, t, vid, X, Y, fx, fy, fz);
+    }
+    if (t >= 0) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float l = B.lam[k];
+            const float l = lam[k];
             c0[k] = l * fx;
             c1[k] = l * fy;
             c2[k] = l * (fz + hz[k]);
