@@ -170,30 +170,50 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 def run_uneven(args):
-    """Uneven batch: 256 meshes (500..200k triangles, 128^2..1024^2), Adam steps of the mask + normal fit."""
+    """Uneven batch: 256 meshes (500..200k triangles, 128^2..1024^2) per GPU, Adam steps of the mask + normal
+    fit.  With N ranks the batch has N x 256 meshes, split by longest-processing-time on T + H*W."""
     import torch
 
-    from paper_2405_02508_gb300 import scenes
+    from paper_2405_02508_gb300 import scenes, shard
     from paper_2405_02508_gb300.fit import UnevenFit
 
-    items = scenes.uneven_batch(n_items=args.items)
+    world, rank, local = shard.env_ranks()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n_all = world * args.items
+    nis, res = scenes.uneven_plan(n_all)
+    costs = [shard.item_cost(8 * n * n, r, r) for n, r in zip(nis, res)]
+    mine = shard.lpt_assign(costs, world)[rank]
+    items = scenes.uneven_batch(n_items=n_all, subset=mine)
     fit = UnevenFit(items, tile=args.tile if args.tile > 0 else 32)
     fit.run(args.warmup)
     torch.cuda.synchronize()
+    shard.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     v = fit.run(args.steps)
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    line = {"metric": METRIC, "value": fit.pixels / (ms * 1e-3) / 1e6, "unit": "Mpix/s", "n_gpus": 1,
+    shard.barrier()
+    ms = shard.max_over_ranks(e0.elapsed_time(e1) / args.steps, "cuda")
+    pixels = sum(r * r for r in res)
+    line = {"metric": METRIC, "value": pixels / (ms * 1e-3) / 1e6, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"uneven batch: {len(items)} meshes, {sum(len(i.tris) for i in items)} tris, "
-                                   f"{fit.pixels / 1e6:.1f} Mpix per step; Adam lr 1e-3, mask + normal L2",
-                       "step": "batched render + micro-edge/interior backward + PyTorch normals and Adam"},
+            "config": {"workload": f"uneven batch: {n_all} meshes, {sum(8 * n * n for n in nis)} tris, "
+                                   f"{pixels / 1e6:.1f} Mpix per step; Adam lr 1e-3, mask + normal L2",
+                       "step": "batched render + micro-edge/interior backward + PyTorch normals and Adam",
+                       "parallelism": f"LPT shards x{world}, no collective"},
             "rmse": {"initial": fit.rmse(fit.v_init), "final": fit.rmse(v), "steps": args.warmup + args.steps}}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
 
 
 def main():
@@ -207,9 +227,9 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2405_02508_gb300 import shard
+
+    world, rank, local = shard.env_ranks()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -221,14 +241,14 @@ def main():
     B.lib()
     dev = "cuda"
     # weak scaling: every rank renders its own batch of views (cameras drawn with a rank-specific seed)
-    scene = scenes.head_multiview(n_views=args.views, seed=6 + rank)
+    scene = scenes.head_multiview(n_views=args.views, seed=shard.view_seed(6, rank))
     n, H, W, C = scene.n_views, scene.H, scene.W, scene.shading.C
     V, T = len(scene.verts), len(scene.tris)
     verts = torch.from_numpy(scene.verts).to(dev)
     attr = torch.from_numpy(scene.attr).to(dev)
     tex = torch.from_numpy(scene.tex).to(dev)
     gen = torch.Generator(device=dev)
-    gen.manual_seed(7 + rank)
+    gen.manual_seed(shard.view_seed(7, rank))
     g = torch.randn((n * H * W, C), generator=gen, device=dev, dtype=torch.float32)
     meshes = [(scene.verts, scene.tris)]
     items = [(0, v, H, W) for v in range(n)]
@@ -252,8 +272,7 @@ def main():
     br.check()
     clocks = ClockSampler(local)
     clocks.start()
-    if world > 1:
-        dist.barrier()
+    shard.barrier()
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -262,15 +281,10 @@ def main():
         br.replay()
     t1.record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    shard.barrier()
     clk = clocks.stop()
     br.check()
-    ms = t0.elapsed_time(t1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = shard.max_over_ranks(t0.elapsed_time(t1) / args.steps, dev)
 
     # per-kernel times: the same step run eagerly with CUDA events around the stages on the launching stream
     ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)] for k in ("fwd", "bwd", "rast")}
@@ -297,8 +311,7 @@ def main():
     h_grad = torch.empty((V, 3), dtype=torch.float32).pin_memory()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
+    shard.barrier()
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
@@ -307,11 +320,7 @@ def main():
         h_grad.copy_(br.grad_verts[:V], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
 
     # plain path: each view its own launch sequence (same kernels, no batching, no graph)
     plain_ms = None

@@ -348,20 +348,30 @@ def head_multiview(n_views: int = 32, H: int = 2048, W: int = 1334, n: int = 128
     return Scene(f"head_{n_views}x{W}x{H}", V, F, cams, H, W, uv, sh, tex=tex, upstream_seed=7)
 
 
-def uneven_batch(n_items: int = 256, seed: int = 8, res_seed: int = 9,
-                 t_min: float = 500.0, t_max: float = 200000.0, resolutions=(128, 256, 512, 1024)):
-    """Uneven batch: ``n_items`` displaced spheres, T log-uniform in [t_min, t_max], res in {128..1024}^2.
-
-    Returns a list of Scenes (one camera each); item i is displaced with seed 1000+i.
-    Channels: normal (3) + mask.
-    """
+def uneven_plan(n_items: int = 256, seed: int = 8, res_seed: int = 9, t_min: float = 500.0,
+                t_max: float = 200000.0, resolutions=(128, 256, 512, 1024)):
+    """Sizes of the uneven batch without building it: per item the octasphere frequency n_i (T = 8 n_i^2) and
+    the square resolution."""
     rng = np.random.default_rng(seed)
     T = np.exp(rng.uniform(math.log(t_min), math.log(t_max), n_items))
     rres = np.random.default_rng(res_seed)
     res = rres.choice(list(resolutions), n_items)
+    n = [max(8, int(round(math.sqrt(T[i] / 8.0)))) for i in range(n_items)]
+    return n, [int(r) for r in res]
+
+
+def uneven_batch(n_items: int = 256, seed: int = 8, res_seed: int = 9,
+                 t_min: float = 500.0, t_max: float = 200000.0, resolutions=(128, 256, 512, 1024), subset=None):
+    """Uneven batch: ``n_items`` displaced spheres, T log-uniform in [t_min, t_max], res in {128..1024}^2.
+
+    Returns a list of Scenes (one camera each); item i is displaced with seed 1000+i.  ``subset``: build only
+    these item indices (a rank's share), in the order given.
+    Channels: normal (3) + mask.
+    """
+    nis, res = uneven_plan(n_items, seed, res_seed, t_min, t_max, resolutions)
     out = []
-    for i in range(n_items):
-        ni = max(8, int(round(math.sqrt(T[i] / 8.0))))
+    for i in (range(n_items) if subset is None else subset):
+        ni = nis[i]
         V, F, P = displaced_sphere(ni, 1000 + i)
         cam = random_direction_camera(3.0, int(res[i]), int(res[i]), np.random.default_rng(2000 + i))
         nrm = vertex_normals(V, F).astype(np.float32)
