@@ -66,8 +66,13 @@ __device__ __forceinline__ int table_slot(int* keys, int vid) {
     unsigned h = ((unsigned)vid * 2654435761u) >> (32 - 9);
 #pragma unroll 1
     for (int probe = 0; probe < kSlots; ++probe) {
-        const int k = atomicCAS(keys + h, -1, vid);
-        if (k == -1 || k == vid) return (int)h;
+        // a slot's key only ever changes from -1 to a vertex id within a tile: a key already seen is final
+        int k = *reinterpret_cast<volatile int*>(keys + h);
+        if (k == vid) return (int)h;
+        if (k == -1) {
+            k = atomicCAS(keys + h, -1, vid);
+            if (k == -1 || k == vid) return (int)h;
+        }
         h = (h + 1) & (kSlots - 1);
     }
     return -1;
@@ -226,13 +231,13 @@ __device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, Bwd
     fz += acc[3 * lane + 2];
 }
 
-// The 32x8 tile (tx, ty) of an item.  All threads of the CTA call it together; it ends with a barrier so
-// the shared buffers can be reused for the next tile.
-// ATTR: also produce the attribute gradients (channels [a0, a0 + A) of each vertex's attribute row, A <= 4:
-// the interpolated channels, or (u, v) in texture mode), aggregated like the vertex gradients.
+// A tile's work is split in three phases separated by CTA barriers: tile_halo (index tile + halo into shared
+// memory), tile_compute (every pixel's gradients, aggregated into the vertex table) and tile_flush (table to
+// global memory, slots cleared for the next tile).  The table starts clear (table_clear once per CTA), and a
+// persistent CTA overlaps the flush of one tile with the halo load of the next.
+
 template <bool ATTR>
-__device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, const BwdArgs& a,
-                                              const float* __restrict__ tex, BwdShared& S, void* ws) {
+__device__ __forceinline__ void table_clear(BwdShared& S) {
     for (int i = threadIdx.x; i < kSlots; i += kThreads) {
         S.skey[i] = -1;
         S.sval[i][0] = 0.f;
@@ -243,21 +248,30 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
             for (int j = 0; j < kMaxA; ++j) S.sattr[i][j] = 0.f;
         }
     }
-    const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
-    const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
+}
+
+__device__ __forceinline__ void tile_halo(const BItem& it, int tx, int ty, BwdShared& S) {
     for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
         const int hy = i / kHW, hx = i % kHW;
         const int gx = tx * kTW + hx - 1, gy = ty * kTH + hy - 1;
         S.sidx[hy][hx] = (gx >= 0 && gx < it.W && gy >= 0 && gy < it.H) ? __ldg(it.index + (size_t)gy * it.W + gx) : -2;
     }
-    __syncthreads();
+}
+
+// The 32x8 tile (tx, ty) of an item, after tile_halo and a barrier.
+// ATTR: also produce the attribute gradients (channels [a0, a0 + A) of each vertex's attribute row, A <= 4:
+// the interpolated channels, or (u, v) in texture mode), aggregated like the vertex gradients.
+template <bool ATTR>
+__device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, const BwdArgs& a,
+                                             const float* __restrict__ tex, BwdShared& S, void* ws) {
+    const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
+    const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
     const int x = tx * kTW + lane, y = ty * kTH + row;
     const int C = a.sh.C;
     const mer_vertex* vb = it.vb;
     const int* tris = it.tris;
     const float* grad = it.grad;
-    const float* image = it.image;
     const float* attr = it.attr;
     float* grad_attr = it.gattr;
     int t = (x < it.W && y < it.H) ? S.sidx[row + 1][lane + 1] : -1;
@@ -450,11 +464,22 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
             }
         }
     }
-    __syncthreads();
+}
+
+// After tile_compute and a barrier: add the table to global memory and clear it.
+template <bool ATTR>
+__device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, BwdShared& S) {
+    const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
+    const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
+    double* gvv = it.gv;
     for (int i = threadIdx.x; i < kSlots; i += kThreads) {
         const int v = S.skey[i];
         if (v < 0) continue;
         const float s0 = S.sval[i][0], s1 = S.sval[i][1], s2 = S.sval[i][2];
+        S.skey[i] = -1;
+        S.sval[i][0] = 0.f;
+        S.sval[i][1] = 0.f;
+        S.sval[i][2] = 0.f;
         if (s0 != 0.f) atomicAdd(gvv + 3 * (size_t)v, (double)s0);
         if (s1 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 1, (double)s1);
         if (s2 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 2, (double)s2);
@@ -463,11 +488,11 @@ __device__ __forceinline__ void backward_tile(const BItem& it, int tx, int ty, c
             for (int j = 0; j < kMaxA; ++j) {
                 if (j >= A) break;
                 const float sa = S.sattr[i][j];
-                if (sa != 0.f) atomicAdd(grad_attr + (size_t)v * a.sh.C_attr + a0 + j, sa);
+                S.sattr[i][j] = 0.f;
+                if (sa != 0.f) atomicAdd(it.gattr + (size_t)v * a.sh.C_attr + a0 + j, sa);
             }
         }
     }
-    __syncthreads();
 }
 
 template <bool ATTR>
@@ -492,7 +517,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __re
     it.gv = grad_vpix + (size_t)view * a.V * 3;
     it.gattr = grad_attr;
     it.V = a.V; it.T = a.T; it.H = a.H; it.W = a.W;
-    backward_tile<ATTR>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
+    table_clear<ATTR>(S);
+    tile_halo(it, local % a.ntx, local / a.ntx, S);
+    __syncthreads();
+    tile_compute<ATTR>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
+    __syncthreads();
+    tile_flush<ATTR>(it, a, S);
 }
 
 // Persistent: each CTA takes the next backward tile of any item from the work queue.
@@ -511,9 +541,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex
     __shared__ long long s_tile;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     const int C = a.sh.C, Ca = a.sh.C_attr;
+    table_clear<ATTR>(S);
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_backward, 1ull);
+    __syncthreads();
+    // Per tile two barriers: after the halo load (thread 0 then takes the next tile id) and before the flush
+    // (the next id is visible after it).  The flush of a tile and the halo load of the next touch disjoint
+    // shared memory, and the next tile's table inserts come only after its first barrier.
     while (true) {
-        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_backward, 1ull);
-        __syncthreads();
         const long long g = s_tile;
         if (g >= btiles) break;
         const mer_item m = items[find_item(items, n_items, g, kFieldBtile)];
@@ -529,7 +563,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex
         it.gv = grad_vpix + 3 * (size_t)m.vrec;
         it.gattr = grad_attr ? grad_attr + (size_t)m.vert * Ca : nullptr;
         it.V = m.V; it.T = m.T; it.H = m.H; it.W = m.W;
-        backward_tile<ATTR>(it, local % ntx, local / ntx, a, tex, S, ws);  // ends with a barrier
+        const int tx = local % ntx, ty = local / ntx;
+        tile_halo(it, tx, ty, S);
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_backward, 1ull);
+        tile_compute<ATTR>(it, tx, ty, a, tex, S, ws);
+        __syncthreads();
+        tile_flush<ATTR>(it, a, S);
     }
 }
 
