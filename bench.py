@@ -292,9 +292,9 @@ def main():
         ev["fwd"][2 * i].record(stream)
         B.mer_batch_project(verts, br.cams, br.items, br.tot, br.vpix)
         ev["rast"][2 * i].record(stream)
-        B.mer_batch_rasterize(br.vpix, br.tris, br.items, br.tot, br.workspace, br.index, None, None, br.persistent_ctas)
+        B.mer_batch_render(br.vpix, br.tris, br.items, br.tot, br.workspace, br.index, attr, tex, br.bg, br.sh,
+                           br.image, None, None, br.persistent_ctas)
         ev["rast"][2 * i + 1].record(stream)
-        B.mer_batch_shade(br.vpix, br.tris, br.items, br.tot, br.index, attr, tex, br.bg, br.sh, br.image, br.workspace)
         ev["fwd"][2 * i + 1].record(stream)
         br.grad_vpix.zero_()
         br.grad_verts.zero_()
@@ -344,7 +344,7 @@ def main():
     peak, peak_kind = peaks()
     bb = backward_bytes_per_launch(n, H, W, C, V)
     achieved = bb / (kms["bwd"] * 1e-3) / 1e9
-    launches_per_step = 10  # project 1, setup/count 1, scan 3, fill 1, raster 1, shade 1, backward 1, proj. backward 1
+    launches_per_step = 9  # project 1, setup/count 1, scan 3, fill 1, raster+shade 1, backward 1, proj. backward 1
     line = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -357,7 +357,7 @@ def main():
         "roofline": {"bound": "hbm", "kernel": "k_backward_batch (fused edge + interior)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "peak_kind": peak_kind, "kernel_ms": kms["bwd"], "algorithmic_bytes": bb},
-        "kernels_ms": {"forward (project+raster+shade)": kms["fwd"], "bin+raster": kms["rast"],
+        "kernels_ms": {"forward (project+raster+shade)": kms["fwd"], "bin+raster+shade (fused)": kms["rast"],
                        "backward": kms["bwd"]},
         "step_algorithmic_gbs": step_bytes(n, H, W, C, V, T, tex.numel() * 4) / (ms * 1e-3) / 1e9,
         "plain": None if plain_ms is None else {"value": px_step / (plain_ms * 1e-3) / 1e6, "unit": "Mpix/s",

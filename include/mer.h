@@ -253,6 +253,16 @@ int mer_batch_shade(const mer_vertex* vpix, const int32_t* tris, const mer_item*
                     const mer_batch_totals* totals, const int32_t* index, const float* attr, const float* tex,
                     const float* bg_host, const mer_shading* shading_host, float* image, void* status_ws,
                     void* stream);
+/* mer_batch_rasterize followed by mer_batch_shade, in one persistent pass: each bin tile is shaded from
+ * its z-buffer winners as soon as it is resolved, so the index image is written but not read back.
+ * Results (index, depth, bary, image) are identical to the two calls; arguments are the union of
+ * theirs, with the device status going to `workspace`.  Supp. B: rasterization, barycentrics and
+ * interpolation modules. */
+int mer_batch_render(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,
+                     const mer_batch_totals* totals, void* workspace, size_t workspace_bytes,
+                     int32_t* index, float* depth, float* bary, const float* attr, const float* tex,
+                     const float* bg_host, const mer_shading* shading_host, float* image, int persistent_ctas,
+                     void* stream);
 int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,
                        const mer_batch_totals* totals, const int32_t* index, const float* image,
                        const float* grad_image, const float* attr, const float* tex,

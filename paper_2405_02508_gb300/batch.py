@@ -71,8 +71,14 @@ class BatchRenderer:
         self.workspace = torch.zeros((nbytes + 255) // 256 * 64, dtype=torch.float32, device=self.device)
 
     # -- stages ------------------------------------------------------------------------------------
-    def forward(self, verts, attr, tex=None, depth=None, bary=None):
+    def forward(self, verts, attr, tex=None, depth=None, bary=None, fused: bool = True):
+        """Project, bin, raster and shade every item.  fused: raster and shade in one persistent pass
+        (mer_batch_render); otherwise mer_batch_rasterize then mer_batch_shade (same results)."""
         B.mer_batch_project(verts, self.cams, self.items, self.tot, self.vpix)
+        if fused:
+            B.mer_batch_render(self.vpix, self.tris, self.items, self.tot, self.workspace, self.index, attr, tex,
+                               self.bg, self.sh, self.image, depth, bary, self.persistent_ctas)
+            return self.image
         B.mer_batch_rasterize(self.vpix, self.tris, self.items, self.tot, self.workspace, self.index, depth, bary,
                               self.persistent_ctas)
         B.mer_batch_shade(self.vpix, self.tris, self.items, self.tot, self.index, attr, tex, self.bg, self.sh,

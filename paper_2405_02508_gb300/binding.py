@@ -69,6 +69,8 @@ _SIGS = {
     "mer_batch_rasterize": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _Z, _P, _P, _P, _I, _P], _I),
     "mer_batch_shade": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P, ctypes.POINTER(MerShading), _P,
                          _P, _P], _I),
+    "mer_batch_render": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _Z, _P, _P, _P, _P, _P, _P,
+                          ctypes.POINTER(MerShading), _P, _I, _P], _I),
     "mer_batch_backward": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P, _P,
                             ctypes.POINTER(MerShading), _I, _P, _P, _P, _I, _P], _I),
     "mer_batch_project_backward": ([_P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P], _I),
@@ -257,6 +259,15 @@ def mer_batch_shade(vpix, tris, items_dev, tot, index, attr, tex, bg, sh: MerSha
     _check(lib().mer_batch_shade(_ptr(vpix), _ptr(tris), _ptr(items_dev), ctypes.byref(tot), _ptr(index), _ptr(attr),
                                  _ptr(tex), ctypes.cast(bgc, ctypes.c_void_p), ctypes.byref(sh), _ptr(image),
                                  _ptr(status_ws), _stream()), "mer_batch_shade")
+
+
+def mer_batch_render(vpix, tris, items_dev, tot, workspace, index, attr, tex, bg, sh: MerShading, image, depth=None,
+                     bary=None, persistent_ctas=0):
+    bgc = (ctypes.c_float * max(1, sh.C))(*[float(x) for x in bg])
+    _check(lib().mer_batch_render(_ptr(vpix), _ptr(tris), _ptr(items_dev), ctypes.byref(tot), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _ptr(index), _ptr(depth), _ptr(bary),
+                                  _ptr(attr), _ptr(tex), ctypes.cast(bgc, ctypes.c_void_p), ctypes.byref(sh),
+                                  _ptr(image), persistent_ctas, _stream()), "mer_batch_render")
 
 
 def mer_batch_backward(vpix, tris, items_dev, tot, index, image, grad_image, attr, tex, sh: MerShading, terms: int,

@@ -22,6 +22,9 @@ extern "C" int mer_launch_backward(const mer_vertex*, int, const int*, int, int,
 extern "C" size_t mer_batch_raster_workspace_size(long long, long long, long long);
 extern "C" int mer_launch_batch_rasterize(const mer_vertex*, const int*, const mer_item*, int, long long, long long, int,
                                           void*, size_t, int*, float*, float*, int, cudaStream_t);
+extern "C" int mer_launch_batch_render(const mer_vertex*, const int*, const mer_item*, int, long long, long long, int,
+                                       void*, size_t, int*, float*, float*, const float*, const float*, const float*,
+                                       const mer_shading*, float*, int, cudaStream_t);
 extern "C" int mer_launch_project_batch(const float*, const mer_camera*, const mer_item*, int, long long, mer_vertex*,
                                         cudaStream_t);
 extern "C" int mer_launch_project_backward_batch(const mer_camera*, const mer_item*, int, long long, const mer_vertex*,
@@ -238,6 +241,22 @@ int mer_batch_shade(const mer_vertex* vpix, const int32_t* tris, const mer_item*
     if (status_ws && !aligned256(status_ws)) return MER_EINVAL;
     return mer_launch_shade_batch(vpix, tris, items, t->n_items, t->pixels, index, attr, tex, bg_host, sh, image,
                                   status_ws, S(stream));
+}
+
+int mer_batch_render(const mer_vertex* vpix, const int32_t* tris, const mer_item* items, const mer_batch_totals* t,
+                     void* workspace, size_t workspace_bytes, int32_t* index, float* depth, float* bary,
+                     const float* attr, const float* tex, const float* bg_host, const mer_shading* sh, float* image,
+                     int persistent_ctas, void* stream) {
+    if (!totals_ok(t, items) || (t->tile != 16 && t->tile != 32 && t->tile != 64) || !shading_ok(sh)) return MER_EINVAL;
+    if (t->pixels == 0) return MER_OK;
+    if (!workspace || !aligned256(workspace) || !index || !image || persistent_ctas < 0) return MER_EINVAL;
+    if (t->trecs > 0 && (!tris || !vpix)) return MER_EINVAL;
+    if (sh->n_main > 0 && !attr) return MER_EINVAL;
+    if (sh->uv_offset >= 0 && !tex) return MER_EINVAL;
+    if (workspace_bytes < mer_batch_raster_workspace_size(t->tiles, t->trecs, 1)) return MER_EINVAL;
+    return mer_launch_batch_render(vpix, tris, items, t->n_items, t->trecs, t->tiles, t->tile, workspace,
+                                   workspace_bytes, index, depth, bary, attr, tex, bg_host, sh, image, persistent_ctas,
+                                   S(stream));
 }
 
 int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_item* items, const mer_batch_totals* t,

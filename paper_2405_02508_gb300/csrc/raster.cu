@@ -15,7 +15,7 @@
 
 #include <mutex>
 
-#include "mer_device.cuh"
+#include "shade_device.cuh"
 
 namespace mer {
 
@@ -28,6 +28,15 @@ struct RItem {
     int ntx, nty;            // bin tiles across / down
     long long tile0;         // first global bin tile of the item
     long long pix0;          // first global pixel of the item
+    long long vert;          // first attribute row of the item's mesh
+};
+
+// Fused shading of the resolved tile (mer_batch_render): the deferred shading arguments and buffers.
+struct ShadeOut {
+    ShadeArgs a;
+    const float* attr;  // attribute rows of all meshes
+    const float* tex;
+    float* image;       // [pixels, C]
 };
 
 __device__ __forceinline__ int floordiv256(int a) { return a >> 8; }  // arithmetic shift = floor
@@ -193,11 +202,14 @@ struct RasterShared {
     unsigned long long zbuf[TS * TS];
 };
 
-template <int TS>
+// SHADE: also shade every pixel of the tile from its z-buffer winner (shade_fragment, as the deferred
+// shading kernels do from the index image).
+template <int TS, bool SHADE>
 __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, const int* __restrict__ offs,
                                             const int* __restrict__ cnts, const int* __restrict__ list,
                                             bool overflow, RasterShared<TS>& S, int* __restrict__ index,
-                                            float* __restrict__ depth, float* __restrict__ bary) {
+                                            float* __restrict__ depth, float* __restrict__ bary,
+                                            const ShadeOut& so, void* ws) {
     const long long tile = it.tile0 + local_tile;
     const int ty = local_tile / it.ntx, tx = local_tile % it.ntx;
     const int ox = tx * TS, oy = ty * TS;
@@ -258,6 +270,10 @@ __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, con
         const int t = key ? (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull)) : -1;
         const size_t p = (size_t)it.pix0 + (size_t)py * it.W + px;
         index[p] = t;
+        if (SHADE)
+            shade_fragment(it.vpix, it.V, it.tris, it.T, t, px, py,
+                           so.attr ? so.attr + (size_t)it.vert * so.a.sh.C_attr : nullptr, so.tex, so.a,
+                           so.image + p * so.a.sh.C, ws);
         if (!depth && !bary) continue;
         float Z = 0.f, b1 = 0.f, b2 = 0.f;
         if (t >= 0) {
@@ -296,6 +312,7 @@ __device__ __forceinline__ RItem view_item(const BinGeom& g, const mer_vertex* v
     it.ntx = g.ntx; it.nty = g.nty;
     it.tile0 = (long long)view * g.tiles_per_view;
     it.pix0 = (long long)view * g.H * g.W;
+    it.vert = 0;
     return it;
 }
 
@@ -329,7 +346,10 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(TriRaster* __restrict
     const long long tile = blockIdx.x;
     const int view = (int)(tile / g.tiles_per_view);
     const int local = (int)(tile % g.tiles_per_view);
-    raster_tile<TS>(view_item(g, vpix, tris, recs, view), local, offs, cnts, list, overflow, S, index, depth, bary);
+    ShadeOut none;
+    none.attr = nullptr; none.tex = nullptr; none.image = nullptr;
+    raster_tile<TS, false>(view_item(g, vpix, tris, recs, view), local, offs, cnts, list, overflow, S, index, depth,
+                           bary, none, ws);
 }
 
 // ---- batched entry: items from a table ----
@@ -350,6 +370,7 @@ __device__ __forceinline__ RItem batch_item(const mer_item& m, int tile, const m
     it.nty = (m.H + tile - 1) / tile;
     it.tile0 = m.tile;
     it.pix0 = m.pix;
+    it.vert = m.vert;
     return it;
 }
 
@@ -373,7 +394,7 @@ __global__ void k_bin_fill_batch(const mer_vertex* __restrict__ vpix, const int*
 }
 
 // Persistent: each CTA takes the next global tile from the work queue until none is left.
-template <int TS>
+template <int TS, bool SHADE>
 __global__ void __launch_bounds__(kRasterThreads) k_raster_batch(TriRaster* __restrict__ recs, BatchGeom b,
                                                                  const int* __restrict__ offs,
                                                                  const int* __restrict__ cnts,
@@ -381,7 +402,8 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_batch(TriRaster* __re
                                                                  const mer_vertex* __restrict__ vpix,
                                                                  const int* __restrict__ tris, void* ws,
                                                                  long long capacity, int* __restrict__ index,
-                                                                 float* __restrict__ depth, float* __restrict__ bary) {
+                                                                 float* __restrict__ depth, float* __restrict__ bary,
+                                                                 ShadeOut so) {
     __shared__ RasterShared<TS> S;
     __shared__ long long s_tile;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
@@ -393,8 +415,8 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_batch(TriRaster* __re
         if (g >= b.tiles) break;
         const int k = find_item(b.items, b.n_items, g, kFieldTile);
         const mer_item m = b.items[k];
-        raster_tile<TS>(batch_item(m, b.tile, vpix, tris, recs), (int)(g - m.tile), offs, cnts, list, overflow, S,
-                        index, depth, bary);  // ends with a barrier: s_tile may be overwritten after it
+        raster_tile<TS, SHADE>(batch_item(m, b.tile, vpix, tris, recs), (int)(g - m.tile), offs, cnts, list, overflow,
+                               S, index, depth, bary, so, ws);  // ends with a barrier: s_tile may be overwritten after it
     }
 }
 
@@ -493,27 +515,41 @@ extern "C" size_t mer_batch_raster_workspace_size(long long tiles, long long tre
     return layout_for(tiles, trecs, capacity).total;
 }
 
-template <int TS>
+template <int TS, bool SHADE>
 static int launch_raster_batch(unsigned grid, TriRaster* recs, BatchGeom b, const int* offs, const int* counts,
                                const int* list, const mer_vertex* vpix, const int* tris, void* hdr, long long capacity,
-                               int* index, float* depth, float* bary, cudaStream_t s) {
+                               int* index, float* depth, float* bary, const ShadeOut& so, cudaStream_t s) {
     if (grid == 0) {
         int per_sm = 0, sms = 0, dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 2;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 2;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_batch<TS>, kRasterThreads, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_batch<TS, SHADE>, kRasterThreads, 0) !=
+            cudaSuccess)
             return 2;
         grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
     }
-    k_raster_batch<TS><<<grid, kRasterThreads, 0, s>>>(recs, b, offs, counts, list, vpix, tris, hdr, capacity, index,
-                                                       depth, bary);
+    k_raster_batch<TS, SHADE><<<grid, kRasterThreads, 0, s>>>(recs, b, offs, counts, list, vpix, tris, hdr, capacity,
+                                                              index, depth, bary, so);
     return 0;
 }
 
-extern "C" int mer_launch_batch_rasterize(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
-                                          long long trecs, long long tiles, int tile, void* ws, size_t ws_bytes,
-                                          int* index, float* depth, float* bary, int persistent_ctas,
-                                          cudaStream_t s) {
+template <bool SHADE>
+static int launch_raster_batch_tile(int tile, unsigned grid, TriRaster* recs, BatchGeom b, const int* offs,
+                                    const int* counts, const int* list, const mer_vertex* vpix, const int* tris,
+                                    void* hdr, long long capacity, int* index, float* depth, float* bary,
+                                    const ShadeOut& so, cudaStream_t s) {
+    switch (tile) {
+        case 16: return launch_raster_batch<16, SHADE>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
+        case 32: return launch_raster_batch<32, SHADE>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
+        case 64: return launch_raster_batch<64, SHADE>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
+        default: return 1;
+    }
+}
+
+// Binning and the persistent raster of all items; with `so`, each resolved tile is shaded in the same pass.
+static int batch_raster(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items, long long trecs,
+                        long long tiles, int tile, void* ws, size_t ws_bytes, int* index, float* depth, float* bary,
+                        const ShadeOut* so, int persistent_ctas, cudaStream_t s) {
     RasterLayout L = layout_for(tiles, trecs, 1);
     if (ws_bytes < L.total) return 1;
     const long long capacity = (long long)((ws_bytes - L.list) / 4);
@@ -535,16 +571,37 @@ extern "C" int mer_launch_batch_rasterize(const mer_vertex* vpix, const int* tri
                                                                         capacity);
     if (tiles > 0) {
         const unsigned grid = persistent_ctas > 0 ? (unsigned)persistent_ctas : 0u;
-        int rc = 1;
-        switch (tile) {
-            case 16: rc = launch_raster_batch<16>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, s); break;
-            case 32: rc = launch_raster_batch<32>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, s); break;
-            case 64: rc = launch_raster_batch<64>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, s); break;
-            default: return 1;
-        }
+        ShadeOut none;
+        none.attr = nullptr; none.tex = nullptr; none.image = nullptr;
+        const int rc = so ? launch_raster_batch_tile<true>(tile, grid, recs, b, offs, counts, list, vpix, tris, hdr,
+                                                           capacity, index, depth, bary, *so, s)
+                          : launch_raster_batch_tile<false>(tile, grid, recs, b, offs, counts, list, vpix, tris, hdr,
+                                                            capacity, index, depth, bary, none, s);
         if (rc) return rc;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+extern "C" int mer_launch_batch_rasterize(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
+                                          long long trecs, long long tiles, int tile, void* ws, size_t ws_bytes,
+                                          int* index, float* depth, float* bary, int persistent_ctas,
+                                          cudaStream_t s) {
+    return batch_raster(vpix, tris, items, n_items, trecs, tiles, tile, ws, ws_bytes, index, depth, bary, nullptr,
+                        persistent_ctas, s);
+}
+
+extern "C" int mer_launch_batch_render(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
+                                       long long trecs, long long tiles, int tile, void* ws, size_t ws_bytes,
+                                       int* index, float* depth, float* bary, const float* attr, const float* tex,
+                                       const float* bg, const mer_shading* sh, float* image, int persistent_ctas,
+                                       cudaStream_t s) {
+    ShadeOut so;
+    so.a = make_shade_args(tex, bg, sh);
+    so.attr = attr;
+    so.tex = tex;
+    so.image = image;
+    return batch_raster(vpix, tris, items, n_items, trecs, tiles, tile, ws, ws_bytes, index, depth, bary, &so,
+                        persistent_ctas, s);
 }
 
 // ---------------------------------------------------------------------------------------------------

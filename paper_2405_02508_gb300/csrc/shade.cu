@@ -8,83 +8,16 @@
 
 #include <cstdint>
 
-#include "mer_device.cuh"
+#include "shade_device.cuh"
 
 namespace mer {
-
-struct ShadeArgs {
-    mer_shading sh;
-    float bg[kMaxC];
-    int tex_stride;  // floats per texel
-    bool tex_vec4;   // stride 4 and 16-byte aligned: 128-bit texel loads
-};
 
 // Pixel (x, y) of an item: vb / tris / attr are the item's bases, p the global pixel.
 __device__ __forceinline__ void shade_pixel(const mer_vertex* __restrict__ vb, int V, const int* __restrict__ tris,
                                             int T, int x, int y, size_t p, const int* __restrict__ index,
                                             const float* __restrict__ attr, const float* __restrict__ tex,
                                             const ShadeArgs& a, float* __restrict__ image, void* ws) {
-    const int C = a.sh.C;
-    float* o = image + (size_t)p * C;
-    const int t = index[p];
-    if (t >= T) set_status(ws, kStatusRange);
-    int i0 = 0, i1 = 0, i2 = 0;
-    bool ok = t >= 0 && t < T;
-    if (ok) {
-        i0 = tris[3 * (size_t)t];
-        i1 = tris[3 * (size_t)t + 1];
-        i2 = tris[3 * (size_t)t + 2];
-        if ((unsigned)i0 >= (unsigned)V || (unsigned)i1 >= (unsigned)V || (unsigned)i2 >= (unsigned)V) {
-            set_status(ws, kStatusRange);
-            ok = false;
-        }
-    }
-    if (!ok) {
-#pragma unroll
-        for (int c = 0; c < kMaxC; ++c)  // static indices keep the arguments out of local memory
-            if (c < C) o[c] = a.bg[c];
-        return;
-    }
-    const VRec v[3] = {load_vrec(vb + i0), load_vrec(vb + i1), load_vrec(vb + i2)};
-    const int vid[3] = {i0, i1, i2};
-    const Bary B = screen_bary(v, x, y);
-    float b[3];
-    const float s = B.lam[0] * v[0].zeta + B.lam[1] * v[1].zeta + B.lam[2] * v[2].zeta;
-    const float is = 1.0f / s;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) b[k] = B.lam[k] * v[k].zeta * is;
-    const int Ca = a.sh.C_attr;
-    if (a.sh.uv_offset < 0) {
-        for (int c = 0; c < a.sh.n_main; ++c) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) acc += b[k] * __ldg(attr + (size_t)vid[k] * Ca + c);
-            o[c] = acc;
-        }
-    } else {
-        float uk[3], vk[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            uk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset);
-            vk[k] = __ldg(attr + (size_t)vid[k] * Ca + a.sh.uv_offset + 1);
-        }
-        const TexCoord cx = tex_coord(uk[0], uk[1], uk[2], b[1], b[2], a.sh.tex_w);
-        const TexCoord cy = tex_coord(vk[0], vk[1], vk[2], b[1], b[2], a.sh.tex_h);
-        const TexTaps taps = tex_taps(a.sh.tex_h, a.sh.tex_w, cx, cy);
-        if (a.sh.n_main <= 4) {
-            float v4[4];
-            tex_values(tex, a.sh.tex_w, a.tex_stride, a.tex_vec4, a.sh.n_main, taps, v4);
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (c < a.sh.n_main) o[c] = v4[c];
-        } else {
-            float vk_[kMaxC];
-            tex_values(tex, a.sh.tex_w, a.tex_stride, false, a.sh.n_main, taps, vk_);
-            for (int c = 0; c < a.sh.n_main && c < kMaxC; ++c) o[c] = vk_[c];
-        }
-    }
-    if (a.sh.mask_ch >= 0) o[a.sh.mask_ch] = 1.0f;
-    if (a.sh.depth_ch >= 0) o[a.sh.depth_ch] = is;
+    shade_fragment(vb, V, tris, T, index[p], x, y, attr, tex, a, image + p * a.sh.C, ws);
 }
 
 __global__ void k_shade(const mer_vertex* __restrict__ vpix, int V, const int* __restrict__ tris, int T, int n, int H,
@@ -114,14 +47,6 @@ __global__ void k_shade_batch(const mer_vertex* __restrict__ vpix, const int* __
 
 using namespace mer;
 
-static ShadeArgs make_shade_args(const float* tex, const float* bg, const mer_shading* sh) {
-    ShadeArgs a;
-    a.sh = *sh;
-    for (int c = 0; c < kMaxC; ++c) a.bg[c] = (bg && c < sh->C) ? bg[c] : 0.f;
-    a.tex_stride = sh->tex_c > 0 ? sh->tex_c : sh->n_main;
-    a.tex_vec4 = a.tex_stride == 4 && tex && (reinterpret_cast<uintptr_t>(tex) & 15u) == 0;
-    return a;
-}
 
 extern "C" int mer_launch_shade_batch(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
                                       long long pixels, const int* index, const float* attr, const float* tex,

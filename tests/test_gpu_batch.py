@@ -56,6 +56,45 @@ def test_batch_equals_multiview_renderer(tile):
                                atol=1e-6 * np.abs(ref.grad_verts).max())
 
 
+@pytest.mark.parametrize("tile", [16, 64])
+def test_fused_render_equals_raster_then_shade(tile):
+    """mer_batch_render (raster + shade in one pass) writes the same index, depth, barycentrics and image as
+    mer_batch_rasterize followed by mer_batch_shade, bit for bit; also with interpolated attributes."""
+    import torch
+
+    from paper_2405_02508_gb300.batch import BatchRenderer
+
+    sc, br, tex = _multiview_batch(n_views=3, H=300, W=260, n=40, tile=tile)
+    verts = torch.from_numpy(sc.verts).cuda()
+    attr = torch.from_numpy(sc.attr).cuda()
+    br.prepare(verts, attr, tex)  # sizes the bin lists
+    P = br.index.numel()
+    out = {}
+    for fused in (False, True):
+        depth = torch.full((P,), -7.0, device="cuda")
+        bary = torch.full((P, 2), -7.0, device="cuda")
+        br.index.fill_(-9)
+        br.image.fill_(-9.0)
+        br.forward(verts, attr, tex, depth, bary, fused=fused)
+        br.check()
+        out[fused] = (br.index.clone(), br.image.clone(), depth, bary)
+    for a, b in zip(out[False], out[True]):
+        assert torch.equal(a, b)
+    its = scenes.uneven_batch(n_items=5, t_max=20000, resolutions=(96, 200))
+    br2 = BatchRenderer([(it.verts, it.tris) for it in its], [(k, k, it.H, it.W) for k, it in enumerate(its)],
+                        np.concatenate([it.cams for it in its]), its[0].shading, 3, None, tile=tile)
+    v2 = torch.from_numpy(np.concatenate([it.verts for it in its])).cuda()
+    a2 = torch.from_numpy(np.concatenate([it.attr for it in its])).cuda()
+    br2.prepare(v2, a2)
+    imgs = []
+    for fused in (False, True):
+        br2.image.fill_(-9.0)
+        br2.forward(v2, a2, fused=fused)
+        br2.check()
+        imgs.append((br2.index.clone(), br2.image.clone()))
+    assert torch.equal(imgs[0][0], imgs[1][0]) and torch.equal(imgs[0][1], imgs[1][1])
+
+
 def test_batch_uneven_items_against_oracle(orc):
     """Items of the uneven batch (different meshes, triangle counts and resolutions) in one batched pass;
     every sampled item matches the oracle at the parity tolerances."""
