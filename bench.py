@@ -31,7 +31,7 @@ METRIC = "raster+micro-edge backward Mpix/s on 1 GB300; % HBM roofline; batched 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=0, help="bin tile; 0 = autotune over 16/32/64")
@@ -104,6 +104,32 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_backward_batch launch, from an ncu capture
+# of the same workload at 4 views (inputs already larger than L2), per pixel of the launch, with the sha256 of
+# the kernel's sources it was taken on: a launch of n views moves n*H*W times this.  It is reported only while
+# the sources are unchanged.
+BACKWARD_TRAFFIC = {"bytes_per_pixel": 22.9099,
+                    "sources_sha256": "3ae07dc3d8cf07bf57b8d405eb27b42beab1c0b61c7986ff0b9c8003b84dcdc2",
+                    "profile": "profiles/ncu_k_backward_batch_head_4x1334x2048.md"}
+
+
+def backward_sources_sha256() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("backward.cu", "mer_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2405_02508_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def backward_traffic(pixels: int):
+    t = BACKWARD_TRAFFIC
+    if t["bytes_per_pixel"] is None or t["sources_sha256"] != backward_sources_sha256():
+        return None
+    return t["bytes_per_pixel"] * pixels
 
 
 def backward_bytes_per_launch(n, H, W, C, V):
@@ -355,7 +381,7 @@ def main():
                    "one CUDA graph per step", "tile": tile, "tile_autotune_ms": tune,
                    "l2": "inputs larger than L2 (images 1.7 GB per step)", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": "k_backward_batch (fused edge + interior)", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": backward_traffic(n * H * W),
                      "peak_kind": peak_kind, "kernel_ms": kms["bwd"], "algorithmic_bytes": bb},
         "kernels_ms": {"forward (project+raster+shade)": kms["fwd"], "bin+raster+shade (fused)": kms["rast"],
                        "backward": kms["bwd"]},
