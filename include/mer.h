@@ -89,6 +89,9 @@ typedef struct mer_shading {
     int C_attr;  /* channels per vertex of `attr` */
     int tex_h, tex_w;
     int tex_c;   /* floats per texel in memory (>= n_main), 0 = n_main */
+    int backface_ch; /* channel of the back-face image (Supp. B): 1 where the visible triangle faces away
+                        from the camera (snapped screen area > 0 with y down), 0 elsewhere; or -1.  It is
+                        constant per triangle, so only the edge term differentiates it. */
 } mer_shading;
 
 /* Terms computed by mer_backward (bit mask). */

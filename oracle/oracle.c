@@ -38,6 +38,8 @@ typedef struct {
     int C_attr;    /* attribute channels per vertex */
     int tex_h, tex_w;
     int tex_c;     /* floats per texel in memory (>= n_main) */
+    int backface_ch; /* channel holding the back-face image (1 where the visible triangle faces away from the
+                        camera, else 0), or -1 */
 } orc_shading;
 
 enum { ORC_VALID_FRONT = 1, ORC_VALID_GUARD = 2, ORC_VALID = 3 };
@@ -354,8 +356,20 @@ static void tex_bilinear(const float* tex, int TH, int TW, int nc, int stride, d
     }
 }
 
+/* Facing of a triangle (Supp. B back-face image).  With the camera looking down +Z, x right and y down, a
+ * triangle whose world normal (v1 - v0) x (v2 - v0) points away from the camera projects with a positive
+ * signed area (x1 - x0)(y2 - y0) - (y1 - y0)(x2 - x0).  Taken on the snapped coordinates, exactly, like the
+ * coverage test. */
+static int back_facing(const int64_t* snap, const int32_t* tri)
+{
+    const int64_t X0 = snap[2 * tri[0]], Y0 = snap[2 * tri[0] + 1];
+    const int64_t X1 = snap[2 * tri[1]], Y1 = snap[2 * tri[1] + 1];
+    const int64_t X2 = snap[2 * tri[2]], Y2 = snap[2 * tri[2] + 1];
+    return (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0) > 0;
+}
+
 /* Shaded channels of one covered pixel as duals in the 9 vertex coordinates. */
-static void shade_pixel_dual(const double* scr, const int32_t* tri, double px, double py,
+static void shade_pixel_dual(const double* scr, const int64_t* snap, const int32_t* tri, double px, double py,
                              const float* attr, const float* tex, const orc_shading* sh, dual* I)
 {
     dual x[3], y[3], z[3];
@@ -388,17 +402,20 @@ static void shade_pixel_dual(const double* scr, const int32_t* tri, double px, d
     }
     if (sh->mask_ch >= 0) I[sh->mask_ch] = dconst(1.0);
     if (sh->depth_ch >= 0) I[sh->depth_ch] = ddiv(dconst(1.0), s);
+    /* a binary image: constant on each triangle, so only the edge term differentiates it */
+    if (sh->backface_ch >= 0) I[sh->backface_ch] = dconst(back_facing(snap, tri) ? 1.0 : 0.0);
 }
 
 /* ------------------------------------------------------------------------
  * Interpolation module + deferred shading (Supp. B): shaded image [H,W,C].
  * ------------------------------------------------------------------------ */
-int orc_shade(const double* scr, const int32_t* tris, const int32_t* index, int H, int W,
+int orc_shade(const double* scr, const int64_t* snap, const int32_t* tris, const int32_t* index, int H, int W,
               const float* attr, const float* tex, const float* bg, const orc_shading* sh,
               double* image /* [H,W,C] */)
 {
     dual I[64];
     if (sh->C > 64) return -1;
+    if (sh->backface_ch >= 0 && !snap) return -1;
     for (int y = 0; y < H; ++y) {
         for (int x = 0; x < W; ++x) {
             size_t p = (size_t)y * W + x;
@@ -407,7 +424,7 @@ int orc_shade(const double* scr, const int32_t* tris, const int32_t* index, int 
                 for (int c = 0; c < sh->C; ++c) image[p * sh->C + c] = bg[c];
                 continue;
             }
-            shade_pixel_dual(scr, tris + 3 * (size_t)t, x + 0.5, y + 0.5, attr, tex, sh, I);
+            shade_pixel_dual(scr, snap, tris + 3 * (size_t)t, x + 0.5, y + 0.5, attr, tex, sh, I);
             for (int c = 0; c < sh->C; ++c) image[p * sh->C + c] = I[c].v;
         }
     }
@@ -476,7 +493,7 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                 int t = index[p];
                 if (t < 0) continue;
                 const int32_t* tri = tris + 3 * (size_t)t;
-                shade_pixel_dual(scr, tri, x + 0.5, y + 0.5, attr, tex, sh, I);
+                shade_pixel_dual(scr, snap, tri, x + 0.5, y + 0.5, attr, tex, sh, I);
                 const float* g = grad_image + p * C;
                 for (int m = 0; m < 3; ++m)
                     for (int q = 0; q < 3; ++q) {

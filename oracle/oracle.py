@@ -42,7 +42,8 @@ class OrcCamera(ctypes.Structure):
 class OrcShading(ctypes.Structure):
     _fields_ = [("n_main", ctypes.c_int), ("C", ctypes.c_int), ("uv_offset", ctypes.c_int),
                 ("mask_ch", ctypes.c_int), ("depth_ch", ctypes.c_int), ("C_attr", ctypes.c_int),
-                ("tex_h", ctypes.c_int), ("tex_w", ctypes.c_int), ("tex_c", ctypes.c_int)]
+                ("tex_h", ctypes.c_int), ("tex_w", ctypes.c_int), ("tex_c", ctypes.c_int),
+                ("backface_ch", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -77,7 +78,7 @@ def lib():
         L.orc_rasterize.restype = i
         L.orc_pixel_values.argtypes = [P, P, P, i, i, P, P, P]
         L.orc_pixel_values.restype = i
-        L.orc_shade.argtypes = [P, P, P, i, i, P, P, P, ctypes.POINTER(OrcShading), P]
+        L.orc_shade.argtypes = [P, P, P, P, i, i, P, P, P, ctypes.POINTER(OrcShading), P]
         L.orc_shade.restype = i
         L.orc_backward.argtypes = [P, P, P, i, P, P, i, i, P, P, P, P, ctypes.POINTER(OrcShading), i, P, P, P, P, P]
         L.orc_texel_ambiguity.argtypes = [P, P, P, i, i, P, ctypes.POINTER(OrcShading), P]
@@ -110,6 +111,7 @@ def shading(sh, C_attr: int, tex: np.ndarray | None) -> OrcShading:
     s.C_attr = C_attr
     s.tex_h, s.tex_w = (tex.shape[0], tex.shape[1]) if tex is not None else (0, 0)
     s.tex_c = tex.shape[2] if tex is not None else 0
+    s.backface_ch = getattr(sh, "backface_ch", -1)
     return s
 
 
@@ -168,14 +170,16 @@ def pixel_values(scr, tris, index):
     return lam, bary, depth
 
 
-def shade(scr, tris, index, attr, sh, tex=None):
+def shade(scr, tris, index, attr, sh, tex=None, snap=None):
+    """Shaded image [H,W,C] f64; ``snap`` (snapped coordinates) is needed for a back-face channel."""
     H, W = index.shape
     attr = np.ascontiguousarray(attr, dtype=np.float32)
     tex = None if tex is None else np.ascontiguousarray(tex, dtype=np.float32)
     bg = np.ascontiguousarray(sh.bg_array())
     s = shading(sh, attr.shape[1], tex)
     img = np.empty((H, W, sh.C))
-    rc = lib().orc_shade(_p(scr), _p(np.ascontiguousarray(tris, dtype=np.int32)),
+    rc = lib().orc_shade(_p(scr), _p(None if snap is None else np.ascontiguousarray(snap, dtype=np.int64)),
+                         _p(np.ascontiguousarray(tris, dtype=np.int32)),
                          _p(np.ascontiguousarray(index, dtype=np.int32)), H, W, _p(attr), _p(tex), _p(bg),
                          ctypes.byref(s), _p(img))
     assert rc == 0
@@ -247,7 +251,7 @@ def render_view(verts, tris, cam, H, W, attr, sh, tex=None) -> ViewResult:
     r.scr, r.snap, r.flags = project(verts, cam)
     r.index, r.tie, _ = rasterize(r.scr, r.snap, r.flags, tris, H, W)
     r.lam, r.bary, r.depth = pixel_values(r.scr, tris, r.index)
-    r.image = shade(r.scr, tris, r.index, attr, sh, tex)
+    r.image = shade(r.scr, tris, r.index, attr, sh, tex, r.snap)
     r.texamb = texel_ambiguity(r.scr, tris, r.index, attr, sh, tex)
     return r
 

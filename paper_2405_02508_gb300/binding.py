@@ -30,7 +30,8 @@ class MerError(RuntimeError):
 class MerShading(ctypes.Structure):
     _fields_ = [("n_main", ctypes.c_int), ("C", ctypes.c_int), ("uv_offset", ctypes.c_int),
                 ("mask_ch", ctypes.c_int), ("depth_ch", ctypes.c_int), ("C_attr", ctypes.c_int),
-                ("tex_h", ctypes.c_int), ("tex_w", ctypes.c_int), ("tex_c", ctypes.c_int)]
+                ("tex_h", ctypes.c_int), ("tex_w", ctypes.c_int), ("tex_c", ctypes.c_int),
+                ("backface_ch", ctypes.c_int)]
 
 
 class MerItem(ctypes.Structure):
@@ -138,6 +139,7 @@ def shading_struct(sh, C_attr: int, tex: torch.Tensor | None) -> MerShading:
     s.C_attr = C_attr
     s.tex_h, s.tex_w = (int(tex.shape[0]), int(tex.shape[1])) if tex is not None else (0, 0)
     s.tex_c = int(tex.shape[2]) if tex is not None else 0
+    s.backface_ch = getattr(sh, "backface_ch", -1)
     return s
 
 

@@ -56,6 +56,8 @@ bool shading_ok(const mer_shading* sh) {
     if (sh->mask_ch >= 0 && sh->mask_ch < sh->n_main) return false;
     if (sh->depth_ch >= 0 && sh->depth_ch < sh->n_main) return false;
     if (sh->mask_ch >= 0 && sh->mask_ch == sh->depth_ch) return false;
+    if (sh->backface_ch >= sh->C || (sh->backface_ch >= 0 && sh->backface_ch < sh->n_main)) return false;
+    if (sh->backface_ch >= 0 && (sh->backface_ch == sh->mask_ch || sh->backface_ch == sh->depth_ch)) return false;
     if (sh->tex_c != 0 && sh->tex_c < sh->n_main) return false;
     if (sh->uv_offset >= 0) {
         if (sh->uv_offset + 2 > sh->C_attr || sh->tex_h < 1 || sh->tex_w < 1) return false;
@@ -146,7 +148,7 @@ int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int 
 int mer_edge_grad_backward(const float* image, const float* grad_image, int C, const int32_t* index,
                            const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
                            int intersections, double* grad_vpix, void* status_ws, void* stream) {
-    mer_shading sh = {0, C, -1, -1, -1, 0, 0, 0, 0};
+    mer_shading sh = {0, C, -1, -1, -1, 0, 0, 0, 0, -1};
     return mer_backward(vpix, V, tris, T, n, H, W, index, image, grad_image, nullptr, nullptr, &sh,
                         MER_EDGE | (intersections ? MER_INTERSECT : 0), grad_vpix, nullptr, status_ws, stream);
 }
@@ -154,7 +156,7 @@ int mer_edge_grad_backward(const float* image, const float* grad_image, int C, c
 int mer_interpolate_backward(const float* attr, int C_attr, const int32_t* tris, int T, const mer_vertex* vpix, int V,
                              const int32_t* index, int n, int H, int W, const float* grad_out, float* grad_attr,
                              double* grad_vpix, void* status_ws, void* stream) {
-    mer_shading sh = {C_attr, C_attr, -1, -1, -1, C_attr, 0, 0, 0};
+    mer_shading sh = {C_attr, C_attr, -1, -1, -1, C_attr, 0, 0, 0, -1};
     return mer_backward(vpix, V, tris, T, n, H, W, index, nullptr, grad_out, attr, nullptr, &sh, MER_INTERIOR,
                         grad_vpix, grad_attr, status_ws, stream);
 }

@@ -91,6 +91,11 @@ __device__ __forceinline__ void shade_fragment(const mer_vertex* __restrict__ vb
     }
     if (a.sh.mask_ch >= 0) o[a.sh.mask_ch] = 1.0f;
     if (a.sh.depth_ch >= 0) o[a.sh.depth_ch] = is;
+    if (a.sh.backface_ch >= 0) {
+        // back-face image: the exact sign of the snapped screen area (positive = facing away, y down)
+        const int64_t area = (int64_t)(v[1].X - v[0].X) * (v[2].Y - v[0].Y) - (int64_t)(v[1].Y - v[0].Y) * (v[2].X - v[0].X);
+        o[a.sh.backface_ch] = area > 0 ? 1.0f : 0.0f;
+    }
 }
 
 }  // namespace mer

@@ -244,7 +244,8 @@ class Shading:
     Channels [0, n_main) hold interpolated attributes (``uv_offset < 0``) or the
     bilinear texture sampled at the interpolated (u, v) = attribute channels
     ``uv_offset, uv_offset + 1``.  ``mask_ch`` / ``depth_ch`` hold the coverage
-    mask and the depth Z, or are -1.  Background pixels take ``bg``.
+    mask and the depth Z, ``backface_ch`` the back-face image (1 where the visible
+    triangle faces away from the camera), or are -1.  Background pixels take ``bg``.
     """
     n_main: int
     C: int
@@ -252,6 +253,7 @@ class Shading:
     mask_ch: int = -1
     depth_ch: int = -1
     bg: list = field(default_factory=list)
+    backface_ch: int = -1
 
     def bg_array(self) -> np.ndarray:
         b = np.zeros(self.C, dtype=np.float32)
@@ -320,6 +322,25 @@ def two_spheres(H: int = 512, W: int = 512, subdiv: int = 5) -> Scene:
     cams = np.stack([look_at_camera((0.0, 0.0, 4.5), H, W)])
     sh = Shading(n_main=3, C=5, mask_ch=3, depth_ch=4, bg=[0, 0, 0, 0, 0])
     return Scene(f"two_spheres_{H}", V.astype(np.float32), T, cams, H, W, nrm, sh, upstream_seed=3)
+
+
+def open_sphere(H: int = 256, W: int = 256, subdiv: int = 4, cap: float = 0.55) -> Scene:
+    """Icosphere (subdivision 4) with the cap of triangles whose centroid has z > ``cap`` removed, seen through
+    the hole from (0.9, 0.6, 2.6): the inner surface shows its back faces.
+
+    Image channels: interpolated vertex normals (3), back-face image, mask.  Upstream N(0,1) seed 5.
+    """
+    P, F = icosphere(subdiv)
+    keep = P[F].mean(axis=1)[:, 2] <= cap
+    used = np.unique(F[keep])
+    remap = -np.ones(len(P), np.int64)
+    remap[used] = np.arange(len(used))
+    V = P[used]
+    T = remap[F[keep]].astype(np.int32)
+    nrm = vertex_normals(V, T).astype(np.float32)
+    cams = np.stack([look_at_camera((0.9, 0.6, 2.6), H, W)])
+    sh = Shading(n_main=3, C=5, backface_ch=3, mask_ch=4, bg=[0, 0, 0, 0, 0])
+    return Scene(f"open_sphere_{H}", V.astype(np.float32), T, cams, H, W, nrm, sh, upstream_seed=5)
 
 
 def head_mesh(n: int = 128, seed: int = 4):

@@ -125,6 +125,20 @@ def test_parity_edge_only_and_interior_only(orc):
     run_parity(orc, sc, sc.upstream(), terms=2)
 
 
+def test_parity_backface_image_and_loss(orc):
+    """Back-face image (Supp. B) of an open sphere seen through its hole, with normals and mask: the channel
+    equals the oracle's bit for bit; the gradients of N(0,1) upstream and of a pure back-face loss
+    (L = sum of the channel: only its edges carry gradient) match the oracle."""
+    sc = scenes.open_sphere(H=256, W=256)
+    gpu, stats, counts = run_parity(orc, sc, sc.upstream(), want_attr=True)
+    bf = gpu.image[..., sc.shading.backface_ch]
+    assert 0.1 < bf[gpu.index >= 0].mean() < 0.95
+    g = np.zeros((1, sc.H, sc.W, sc.shading.C), np.float32)
+    g[..., sc.shading.backface_ch] = 1.0
+    gpu2, _, counts2 = run_parity(orc, sc, g)
+    assert np.abs(gpu2.grad_verts).max() > 0
+
+
 @pytest.mark.parametrize("store_bary", [True, False])
 def test_parity_head_single_view(orc, store_bary):
     """1024^2, 131k triangles, bilinear texture through interpolated UVs, RGB + mask."""

@@ -27,6 +27,8 @@ MUTATIONS = {
     "top_left_rule": ("if (!(ga > 0 || (ga == 0 && gb > 0))) return 0;", "if (!(ga >= 0)) return 0;"),
     "depth_tie_break": ("(z == z1[p] && t < index[p])", "(z == z1[p] && t > index[p])"),
     "projection_operand": ("xs = (cam->fx * Xc) * zeta + cam->cx;", "xs = (cam->fx * Yc) * zeta + cam->cx;"),
+    "backface_sign": ("return (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0) > 0;",
+                      "return (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0) < 0;"),
     "project_backward_transpose": ("grad_verts[3 * v + 0] += R[0] * gX + R[3] * gY + R[6] * gZ;",
                                    "grad_verts[3 * v + 0] += R[0] * gX + R[1] * gY + R[2] * gZ;"),
 }

@@ -602,3 +602,77 @@ def test_p7_coplanar_shared_edge_is_adjacent(orc):
     s2 = flat_scene(orc, [[5.2, 5.1, 0.5], [34.7, 6.3, 0.5], [6.1, 33.9, 0.5], [35.3, 34.6, 0.5]],
                     [[0, 1, 3], [0, 3, 2]], N, N, [0.6] * 4, 0.2)
     np.testing.assert_array_equal(s2[4] >= 0, index >= 0)
+
+
+# ---------------------------------------------------------------------------
+# Back-face image (Supp. B): a binary channel differentiable only through its edges
+# ---------------------------------------------------------------------------
+
+def _world_back_facing(sc):
+    """Independent facing test in world space: the normal (v1 - v0) x (v2 - v0) points away from the camera."""
+    cam = sc.cams[0]
+    R = np.asarray(cam["R"], np.float64).reshape(3, 3)
+    t = np.asarray(cam["t"], np.float64).reshape(3)
+    centre = -R.T @ t
+    V = sc.verts.astype(np.float64)
+    F = sc.tris
+    n = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+    return (n * (centre - V[F[:, 0]])).sum(axis=1) < 0
+
+
+def test_backface_image_matches_world_normals(orc):
+    """Open sphere seen through its hole: the back-face channel is 1 exactly on the pixels whose visible triangle
+    faces away from the camera in world space, 0 on the others and on the background; both kinds occur."""
+    sc = scenes.open_sphere(H=128, W=128)
+    r = orc.render(sc)[0]
+    cov = r.index >= 0
+    bf = _world_back_facing(sc)
+    ch = r.image[..., sc.shading.backface_ch]
+    np.testing.assert_array_equal(ch[cov], bf[r.index[cov]].astype(np.float64))
+    assert np.all(ch[~cov] == 0.0)
+    assert 0.1 < ch[cov].mean() < 0.95
+
+
+def test_backface_closed_sphere_outside_and_inside(orc):
+    """A closed outward-oriented sphere shows no back face from outside and only back faces from inside."""
+    P, F = scenes.icosphere(3)
+    sh = Shading(n_main=0, C=2, backface_ch=0, mask_ch=1, bg=[0, 0])
+    attr = np.zeros((len(P), 1), np.float32)
+    for eye, expect in (((0.3, 0.4, 3.0), 0.0), ((0.05, -0.03, 0.1), 1.0)):
+        cam = scenes.look_at_camera(eye, 64, 64, target=(0.3, 0.2, 1.0) if expect else (0.0, 0.0, 0.0))
+        r = orc.render_view(P.astype(np.float32), F, cam, 64, 64, attr, sh)
+        cov = r.index >= 0
+        assert cov.mean() > 0.3
+        assert np.all(r.image[..., 0][cov] == expect)
+
+
+@pytest.mark.parametrize("winding", [(0, 1, 2), (0, 2, 1)])
+def test_backface_loss_ramp_identity(orc, winding):
+    """L = sum_p x_p B_p on the back-face channel of one triangle: the x gradients sum to #covered when the
+    triangle faces away (B = 1 inside, 0 outside: the P1 identity with c - bg = 1) and vanish when it faces
+    the camera (B = 0 everywhere); no interior term in either case."""
+    H, W = 40, 48
+    pts = [[5.3, 4.1, 0.5], [41.7, 9.9, 0.5], [17.2, 35.6, 0.5]]
+    scr, snap, flags = orc.snap_screen(np.asarray(pts, dtype=np.float64))
+    tris = np.asarray([winding], dtype=np.int32)
+    index, _, _ = orc.rasterize(scr, snap, flags, tris, H, W)
+    sh = Shading(n_main=0, C=1, backface_ch=0, bg=[0.0])
+    attr = np.zeros((3, 1), np.float32)
+    image = orc.shade(scr, tris, index, attr, sh, snap=snap)
+    X, Y = snap[:, 0].astype(np.int64), snap[:, 1].astype(np.int64)
+    a, b, c = winding
+    area = (X[b] - X[a]) * (Y[c] - Y[a]) - (Y[b] - Y[a]) * (X[c] - X[a])
+    facing_away = area > 0  # y down: positive screen area = clockwise on the page
+    yy, xx = np.mgrid[0:H, 0:W] + 0.5
+    g = xx[..., None].astype(np.float32)
+    gs, _, _ = orc.backward(scr, snap, flags, tris, index, image, g, attr, sh, mode=ALL)
+    ncov = int((index >= 0).sum())
+    assert ncov > 100
+    if facing_away:
+        assert np.all(image[..., 0][index >= 0] == 1.0)
+        assert gs[:, 0].sum() == pytest.approx(ncov, rel=1e-12)
+    else:
+        assert np.all(image == 0.0)
+        assert np.all(gs == 0.0)
+    gi, _, _ = orc.backward(scr, snap, flags, tris, index, image, g, attr, sh, mode=INTERIOR)
+    assert np.all(gi == 0.0)
