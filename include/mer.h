@@ -276,6 +276,33 @@ int mer_batch_project_backward(const mer_camera* cams, const mer_item* items, co
                                const mer_vertex* vpix, const double* grad_vpix, float* grad_verts,
                                void* stream);
 
+/* ---- Laplacian preconditioning of vertex updates (Nicolet et al. 2021, used by the paper for every mesh
+ * optimisation: Sec. 5, Supp. B, lambda = 16) ----
+ * Positions x [V,3] are reparameterised as u = M x, M = I + lambda L, with L the combinatorial Laplacian of
+ * the edge graph of all meshes (L_ii = number of distinct neighbours of vertex i, L_ij = -1 for every edge;
+ * meshes are independent blocks).  An optimiser steps u with the gradient M^-1 dL/dx and maps back with
+ * x = M^-1 u. */
+
+/* Host call (host pointers): the edge graph of triangles [T,3] over V vertices in CSR form.  row_ptr
+ * [V+1] is always written (row_ptr[V] = number of directed edges); col [row_ptr[V]] (neighbours of each
+ * vertex, ascending) only when not NULL, so a first call with col = NULL sizes it.  Degenerate triangle
+ * edges (a == b) are skipped.  MER_ERANGE if a vertex id is outside [0, V). */
+int mer_laplacian_csr(const int32_t* tris, int64_t T, int64_t V, int64_t* row_ptr, int32_t* col);
+/* y = (I + lambda L) x, x and y [V,3] float32 on the device (distinct buffers). */
+int mer_precond_apply(const int64_t* row_ptr, const int32_t* col, int64_t V, float lambda, const float* x,
+                      float* y, void* stream);
+size_t mer_precond_solve_workspace_size(int64_t V);
+/* Solve (I + lambda L) x = b by conjugate gradients on the device (FP32 vectors, FP64 dot products), the
+ * three columns as one block-diagonal system.  x holds the initial guess (a warm start) and receives the
+ * solution.  Runs at most max_iters iterations as a fixed launch sequence; the iterations after the
+ * residual norm falls to rel_tol * |b| return immediately.  workspace: 256-byte aligned device memory of
+ * mer_precond_solve_workspace_size(V) bytes, owned by the caller. */
+int mer_precond_solve(const int64_t* row_ptr, const int32_t* col, int64_t V, float lambda, const float* b,
+                      float* x, int max_iters, float rel_tol, void* workspace, size_t workspace_bytes,
+                      void* stream);
+/* Synchronises `stream` and reports the last solve in `workspace`: iterations run and |r| / |b|. */
+int mer_precond_solve_info(const void* workspace, int* iters, double* rel_residual, void* stream);
+
 /* Synchronises `stream`, reads and clears the device status word of a
  * workspace (or of a status buffer of at least 256 bytes passed as status_ws to
  * the other calls).  Returns MER_OK, MER_EOVERFLOW or MER_ERANGE; *total_bins

@@ -63,6 +63,11 @@ _SIGS = {
     "mer_interpolate_backward": ([_P, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "mer_project_backward": ([_I, _P, _I, _P, _P, _P, _P], _I),
     "mer_sync_status": ([_P, ctypes.POINTER(ctypes.c_int64), _P], _I),
+    "mer_laplacian_csr": ([_P, ctypes.c_int64, ctypes.c_int64, _P, _P], _I),
+    "mer_precond_apply": ([_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P], _I),
+    "mer_precond_solve_workspace_size": ([ctypes.c_int64], _Z),
+    "mer_precond_solve": ([_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _I, ctypes.c_float, _P, _Z, _P], _I),
+    "mer_precond_solve_info": ([_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _P], _I),
     "mer_rasterize_noalloc": ([_P, _I, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "mer_batch_plan": ([_P, _I, _I, ctypes.POINTER(MerBatchTotals)], _I),
     "mer_batch_workspace_size": ([ctypes.POINTER(MerBatchTotals), _L], _Z),
@@ -219,6 +224,38 @@ def mer_sync_status(workspace) -> tuple[int, int]:
     tot = ctypes.c_int64(0)
     code = lib().mer_sync_status(_ptr(workspace), ctypes.byref(tot), _stream())
     return code, int(tot.value)
+
+
+def mer_laplacian_csr(tris: np.ndarray, V: int) -> tuple[np.ndarray, np.ndarray]:
+    """Host call: (row_ptr [V+1] int64, col [nnz] int32) of the meshes' edge graph."""
+    tris = np.ascontiguousarray(tris, dtype=np.int32)
+    row_ptr = np.zeros(V + 1, dtype=np.int64)
+    tp = tris.ctypes.data_as(ctypes.c_void_p) if tris.size else None
+    _check(lib().mer_laplacian_csr(tp, len(tris), V, row_ptr.ctypes.data_as(ctypes.c_void_p), None),
+           "mer_laplacian_csr")
+    col = np.zeros(max(int(row_ptr[-1]), 1), dtype=np.int32)
+    _check(lib().mer_laplacian_csr(tp, len(tris), V, row_ptr.ctypes.data_as(ctypes.c_void_p),
+                                   col.ctypes.data_as(ctypes.c_void_p)), "mer_laplacian_csr")
+    return row_ptr, col[: int(row_ptr[-1])]
+
+
+def mer_precond_apply(row_ptr, col, lam: float, x, y):
+    _check(lib().mer_precond_apply(_ptr(row_ptr), _ptr(col), x.shape[0], float(lam), _ptr(x), _ptr(y), _stream()),
+           "mer_precond_apply")
+
+
+def mer_precond_solve(row_ptr, col, lam: float, b, x, max_iters: int, rel_tol: float, workspace):
+    _check(lib().mer_precond_solve(_ptr(row_ptr), _ptr(col), b.shape[0], float(lam), _ptr(b), _ptr(x), max_iters,
+                                   float(rel_tol), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                   _stream()), "mer_precond_solve")
+
+
+def mer_precond_solve_info(workspace) -> tuple[int, float]:
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    _check(lib().mer_precond_solve_info(_ptr(workspace), ctypes.byref(it), ctypes.byref(res), _stream()),
+           "mer_precond_solve_info")
+    return int(it.value), float(res.value)
 
 
 def mer_rasterize_noalloc(vpix, tris, H, W, tile, index, depth=None, bary=None, status=None):

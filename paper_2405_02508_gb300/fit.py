@@ -65,7 +65,22 @@ class UnevenFit:
     def pixels(self) -> int:
         return int(self.br.tot.pixels)
 
+    @torch.no_grad()
+    def loss(self, x: torch.Tensor) -> float:
+        """The mask + normal L2 loss at positions x."""
+        self.br.forward(x.contiguous(), vertex_normals(x, self.tris_global).contiguous())
+        return float(((self.br.image - self.target) ** 2).sum())
+
+    def loss_grad(self, x: torch.Tensor) -> torch.Tensor:
+        """dL/dx of the mask + normal L2 loss at positions x (renderer + PyTorch normals)."""
+        verts = x.detach().requires_grad_(True)
+        img = BatchRender.apply(verts, vertex_normals(verts, self.tris_global), self.br)
+        loss = ((img - self.target) ** 2).sum()
+        loss.backward()
+        return verts.grad
+
     def run(self, steps: int, lr: float = 1e-3):
+        """Plain per-vertex Adam on the positions."""
         verts = self.v_init.clone().requires_grad_(True)
         opt = torch.optim.Adam([verts], lr=lr)
         for _ in range(steps):
@@ -75,6 +90,28 @@ class UnevenFit:
             loss.backward()
             opt.step()
         return verts.detach()
+
+    def run_preconditioned(self, steps: int, lr: float = 1e-2, lam: float = 16.0, x0: torch.Tensor | None = None):
+        """Large-steps loop: uniform Adam on u = (I + lam L) x, gradients and positions through the device
+        solves (both warm-started)."""
+        from .precond import LaplacianPreconditioner, UniformAdam
+
+        if getattr(self, "_precond", None) is None or self._precond.lam != lam:
+            tris = self.tris_global.cpu().numpy().astype(np.int32)
+            self._precond = LaplacianPreconditioner(tris, len(self.v_true), lam)
+            block = np.concatenate([np.full(self.vert_off[k + 1] - self.vert_off[k], k)
+                                    for k in range(len(self.items))])
+            self._block = torch.from_numpy(block).cuda()
+        P = self._precond
+        x = (self.v_init if x0 is None else x0).clone()
+        u = P.apply(x)
+        opt = UniformAdam(u, self._block, len(self.items), lr)
+        gu = torch.zeros_like(x)
+        for _ in range(steps):
+            gu = P.solve(self.loss_grad(x), gu)
+            opt.step(gu)
+            x = P.solve(u, x)
+        return x
 
     def rmse(self, verts, subset=None) -> float:
         d = (verts - self.v_true).double()
