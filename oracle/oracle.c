@@ -696,3 +696,157 @@ void orc_project_backward(const float* verts, int V, const orc_camera* cam, cons
         grad_verts[3 * v + 2] += R[2] * gX + R[5] * gY + R[8] * gZ;
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Forward gradients (Sec. 5, "forward gradients"): the per-pixel derivative of
+ * the shaded image with respect to one scene parameter theta, given the
+ * parameter's effect on the projected vertices, tangent[V,3] =
+ * d(x_s, y_s, zeta)/d theta.  It is the transpose of orc_backward's linear
+ * map: for every cotangent image g, sum_p g_p . out_p = sum_v grad_scr_v . tangent_v.
+ *
+ * Interior: the 9 vertex derivatives of the pixel's dual-number shading dotted
+ * with its vertices' tangents.  Edge: a scattering pair (A, B) (same
+ * classification as orc_backward) with micro-edge position p (increasing from
+ * A to B) moves by dp/dtheta; Eq. 11 says that changes I_A and I_B each by
+ * 1/2 (I_A - I_B) dp/dtheta.  The moving fragment is r = sum_i lambda_i v_i at
+ * its pixel centre, so dr/dtheta = sum_i lambda_i tangent_i; overhang:
+ * dp/dtheta = the pair-axis component of the foreground fragment's dr;
+ * intersection: the sum over both fragments of Eq. 12's dp/dr times the slice
+ * normal n^v dotted with that fragment's (axis, zeta) motion.
+ * out and out_abs (the sum of the magnitudes of every term, or NULL) are
+ * [H,W,C] and accumulated.
+ * ------------------------------------------------------------------------ */
+static void frag_tangent(const double* scr, const int32_t* tris, int t, int x, int y, const double* tangent,
+                         double dr[3], double dr_abs[3])
+{
+    const int32_t* tri = tris + 3 * (size_t)t;
+    double lam[3];
+    screen_lambda(scr, tri, x + 0.5, y + 0.5, lam);
+    for (int q = 0; q < 3; ++q) {
+        dr[q] = 0.0;
+        dr_abs[q] = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            dr[q] += lam[i] * tangent[3 * (size_t)tri[i] + q];
+            dr_abs[q] += fabs(lam[i] * tangent[3 * (size_t)tri[i] + q]);
+        }
+    }
+}
+
+int orc_forward_grad(const double* scr, const int64_t* snap, const int32_t* flags, int V,
+                     const int32_t* tris, const int32_t* index, int H, int W,
+                     const double* image /* [H,W,C] */, const float* attr, const float* tex,
+                     const orc_shading* sh, int mode, const double* tangent /* [V,3] */,
+                     double* out /* [H,W,C] */, double* out_abs /* [H,W,C] or NULL */)
+{
+    const int C = sh->C;
+    dual I[64];
+    if (C > 64) return -1;
+    (void)V;
+    if (mode & ORC_INTERIOR) {
+        for (int y = 0; y < H; ++y) {
+            for (int x = 0; x < W; ++x) {
+                size_t p = (size_t)y * W + x;
+                int t = index[p];
+                if (t < 0) continue;
+                const int32_t* tri = tris + 3 * (size_t)t;
+                shade_pixel_dual(scr, snap, tri, x + 0.5, y + 0.5, attr, tex, sh, I);
+                for (int c = 0; c < C; ++c) {
+                    double acc = 0.0, mag = 0.0;
+                    for (int m = 0; m < 3; ++m)
+                        for (int q = 0; q < 3; ++q) {
+                            const double tq = tangent[3 * (size_t)tri[m] + q];
+                            acc += I[c].d[3 * m + q] * tq;
+                            mag += I[c].m[3 * m + q] * fabs(tq);
+                        }
+                    out[p * C + c] += acc;
+                    if (out_abs) out_abs[p * C + c] += mag;
+                }
+            }
+        }
+    }
+    if (!(mode & ORC_EDGE)) return 0;
+    for (int axis = 0; axis < 2; ++axis) {
+        int dx = axis == 0 ? 1 : 0, dy = axis == 0 ? 0 : 1;
+        for (int y = 0; y + dy < H; ++y) {
+            for (int x = 0; x + dx < W; ++x) {
+                int xa = x, ya = y, xb = x + dx, yb = y + dy;
+                size_t pa = (size_t)ya * W + xa, pb = (size_t)yb * W + xb;
+                int ta = index[pa], tb = index[pb];
+                if (ta == tb) continue;
+                double dpdt = 0.0, dpdt_abs = 0.0;
+                int fg = -1;
+                if (ta < 0 || tb < 0) {
+                    fg = ta >= 0 ? 0 : 1;
+                } else {
+                    int b_in_a = orc_covers_pixel(snap, flags, tris, ta, xb, yb);
+                    int a_in_b = orc_covers_pixel(snap, flags, tris, tb, xa, ya);
+                    if (!b_in_a && !a_in_b) continue;
+                    if (b_in_a && a_in_b) {
+                        if (!(mode & ORC_INTERSECT)) continue;
+                        double NA[3], NB[3];
+                        tri_normal(scr, tris + 3 * (size_t)ta, NA);
+                        tri_normal(scr, tris + 3 * (size_t)tb, NB);
+                        double nA[2] = {NA[axis], NA[2]}, nB[2] = {NB[axis], NB[2]};
+                        double den_a = nB[0] * nA[1] - nB[1] * nA[0];
+                        double mag = hypot(nA[0], nA[1]) * hypot(nB[0], nB[1]);
+                        if (fabs(den_a) <= 1e-12 * mag) continue;
+                        double dpdr_a = -nB[1] / den_a;
+                        double den_b = nA[0] * nB[1] - nA[1] * nB[0];
+                        double dpdr_b = -nA[1] / den_b;
+                        double dra[3], drb[3], dra_abs[3], drb_abs[3];
+                        frag_tangent(scr, tris, ta, xa, ya, tangent, dra, dra_abs);
+                        frag_tangent(scr, tris, tb, xb, yb, tangent, drb, drb_abs);
+                        dpdt = dpdr_a * (nA[0] * dra[axis] + nA[1] * dra[2]) +
+                               dpdr_b * (nB[0] * drb[axis] + nB[1] * drb[2]);
+                        dpdt_abs = fabs(dpdr_a) * (fabs(nA[0]) * dra_abs[axis] + fabs(nA[1]) * dra_abs[2]) +
+                                   fabs(dpdr_b) * (fabs(nB[0]) * drb_abs[axis] + fabs(nB[1]) * drb_abs[2]);
+                    } else {
+                        fg = a_in_b ? 0 : 1;
+                    }
+                }
+                if (fg >= 0) {
+                    double dr[3], dr_abs[3];
+                    if (fg == 0) frag_tangent(scr, tris, ta, xa, ya, tangent, dr, dr_abs);
+                    else frag_tangent(scr, tris, tb, xb, yb, tangent, dr, dr_abs);
+                    dpdt = dr[axis];
+                    dpdt_abs = dr_abs[axis];
+                }
+                for (int c = 0; c < C; ++c) {
+                    const double h = 0.5 * (image[pa * C + c] - image[pb * C + c]);
+                    out[pa * C + c] += h * dpdt;
+                    out[pb * C + c] += h * dpdt;
+                    if (out_abs) {
+                        const double hm = 0.5 * (fabs(image[pa * C + c]) + fabs(image[pb * C + c])) * dpdt_abs;
+                        out_abs[pa * C + c] += hm;
+                        out_abs[pb * C + c] += hm;
+                    }
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/* Tangent of the projected vertices, d(x_s, y_s, zeta) = J(X_c) R d(X_w), for a world-space vertex tangent
+ * (the forward counterpart of orc_project_backward); vertices at or before the near plane get 0. */
+void orc_project_jvp(const float* verts, int V, const orc_camera* cam, const double* tangent_world,
+                     double* tangent_scr /* [V,3] */)
+{
+    const double* R = cam->R;
+    for (int v = 0; v < V; ++v) {
+        double x = verts[3 * v + 0], y = verts[3 * v + 1], z = verts[3 * v + 2];
+        double Xc = ((R[0] * x + R[1] * y) + R[2] * z) + cam->t[0];
+        double Yc = ((R[3] * x + R[4] * y) + R[5] * z) + cam->t[1];
+        double Zc = ((R[6] * x + R[7] * y) + R[8] * z) + cam->t[2];
+        double* o = tangent_scr + 3 * (size_t)v;
+        if (!(Zc > cam->znear)) { o[0] = o[1] = o[2] = 0.0; continue; }
+        const double* d = tangent_world + 3 * (size_t)v;
+        double dX = R[0] * d[0] + R[1] * d[1] + R[2] * d[2];
+        double dY = R[3] * d[0] + R[4] * d[1] + R[5] * d[2];
+        double dZ = R[6] * d[0] + R[7] * d[1] + R[8] * d[2];
+        double iz = 1.0 / Zc;
+        o[0] = cam->fx * (dX * Zc - Xc * dZ) * iz * iz;
+        o[1] = cam->fy * (dY * Zc - Yc * dZ) * iz * iz;
+        o[2] = -dZ * iz * iz;
+    }
+}

@@ -86,6 +86,10 @@ def lib():
         L.orc_backward.restype = i
         L.orc_project_backward.argtypes = [P, i, ctypes.POINTER(OrcCamera), P, P]
         L.orc_project_backward.restype = None
+        L.orc_forward_grad.argtypes = [P, P, P, i, P, P, i, i, P, P, P, ctypes.POINTER(OrcShading), i, P, P, P]
+        L.orc_forward_grad.restype = i
+        L.orc_project_jvp.argtypes = [P, i, ctypes.POINTER(OrcCamera), P, P]
+        L.orc_project_jvp.restype = None
         _lib = L
     return _lib
 
@@ -227,6 +231,35 @@ def texel_ambiguity(scr, tris, index, attr, sh, tex):
                               _p(np.ascontiguousarray(index, dtype=np.int32)), H, W, _p(attr), ctypes.byref(s),
                               _p(out))
     return out.astype(bool)
+
+
+def forward_grad(scr, snap, flags, tris, index, image, tangent, attr, sh, tex=None,
+                 mode: int = EDGE | INTERIOR | INTERSECT, want_abs: bool = False):
+    """Forward gradient image [H,W,C] f64 for the projected-vertex tangent [V,3] (+ the magnitude image)."""
+    H, W = index.shape
+    attr = np.ascontiguousarray(attr, dtype=np.float32)
+    tex = None if tex is None else np.ascontiguousarray(tex, dtype=np.float32)
+    image = np.ascontiguousarray(image, dtype=np.float64)
+    s = shading(sh, attr.shape[1], tex)
+    out = np.zeros((H, W, sh.C))
+    mag = np.zeros((H, W, sh.C)) if want_abs else None
+    rc = lib().orc_forward_grad(_p(scr), _p(np.ascontiguousarray(snap, dtype=np.int64)),
+                                _p(np.ascontiguousarray(flags, dtype=np.int32)), len(scr),
+                                _p(np.ascontiguousarray(tris, dtype=np.int32)),
+                                _p(np.ascontiguousarray(index, dtype=np.int32)), H, W, _p(image), _p(attr), _p(tex),
+                                ctypes.byref(s), mode, _p(np.ascontiguousarray(tangent, dtype=np.float64)), _p(out),
+                                _p(mag))
+    assert rc == 0
+    return (out, mag) if want_abs else out
+
+
+def project_jvp(verts, cam, tangent_world):
+    verts = np.ascontiguousarray(verts, dtype=np.float32)
+    c = camera(cam)
+    out = np.zeros((len(verts), 3))
+    lib().orc_project_jvp(_p(verts), len(verts), ctypes.byref(c),
+                          _p(np.ascontiguousarray(tangent_world, dtype=np.float64)), _p(out))
+    return out
 
 
 def project_backward(verts, cam, grad_scr):

@@ -29,6 +29,10 @@ MUTATIONS = {
     "projection_operand": ("xs = (cam->fx * Xc) * zeta + cam->cx;", "xs = (cam->fx * Yc) * zeta + cam->cx;"),
     "backface_sign": ("return (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0) > 0;",
                       "return (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0) < 0;"),
+    "forward_grad_half": ("const double h = 0.5 * (image[pa * C + c] - image[pb * C + c]);",
+                          "const double h = 1.0 * (image[pa * C + c] - image[pb * C + c]);"),
+    "forward_grad_axis": ("dpdt = dr[axis];", "dpdt = dr[1 - axis];"),
+    "project_jvp_depth": ("o[2] = -dZ * iz * iz;", "o[2] = dZ * iz * iz;"),
     "project_backward_transpose": ("grad_verts[3 * v + 0] += R[0] * gX + R[3] * gY + R[6] * gZ;",
                                    "grad_verts[3 * v + 0] += R[0] * gX + R[1] * gY + R[2] * gZ;"),
 }
@@ -47,6 +51,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                     str(mutated), "-lm"], check=True)
     env = dict(os.environ, ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_forward.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"
