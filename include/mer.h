@@ -276,6 +276,22 @@ int mer_batch_project_backward(const mer_camera* cams, const mer_item* items, co
                                const mer_vertex* vpix, const double* grad_vpix, float* grad_verts,
                                void* stream);
 
+/* Forward gradients (Sec. 5): out [n,H,W,C] = the derivative of the shaded image along one scene
+ * parameter whose effect on the projected vertices is tangent [n,V,3] = d(x_s, y_s, zeta)/d theta (FP32).
+ * The exact transpose of mer_backward with the same terms: interior through the barycentrics,
+ * interpolation / texture and depth; edge: every pair classified as in mer_backward moves its micro-edge
+ * by dp/dtheta (the pair-axis motion of the foreground fragment, or Eq. 12 summed over both fragments
+ * of an intersection) and, by Eq. 11, both of its pixels change by 1/2 (I_A - I_B) dp/dtheta.  out is
+ * overwritten.  Errors as mer_backward. */
+int mer_forward_grad(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
+                     const int32_t* index, const float* image, const float* tangent, const float* attr,
+                     const float* tex, const mer_shading* shading_host, int terms, float* out, void* status_ws,
+                     void* stream);
+/* tangent_vpix [n,V,3] = J(X_c) R tangent_world [V,3] for every view (the tangent map of mer_project;
+ * vertices behind the near plane get 0). */
+int mer_project_jvp(const float* tangent_world, int V, const mer_camera* cams, int n, const mer_vertex* vpix,
+                    float* tangent_vpix, void* stream);
+
 /* ---- Laplacian preconditioning of vertex updates (Nicolet et al. 2021, used by the paper for every mesh
  * optimisation: Sec. 5, Supp. B, lambda = 16) ----
  * Positions x [V,3] are reparameterised as u = M x, M = I + lambda L, with L the combinatorial Laplacian of

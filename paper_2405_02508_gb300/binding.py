@@ -63,6 +63,9 @@ _SIGS = {
     "mer_interpolate_backward": ([_P, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "mer_project_backward": ([_I, _P, _I, _P, _P, _P, _P], _I),
     "mer_sync_status": ([_P, ctypes.POINTER(ctypes.c_int64), _P], _I),
+    "mer_forward_grad": ([_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P, ctypes.POINTER(MerShading), _I, _P, _P,
+                          _P], _I),
+    "mer_project_jvp": ([_P, _I, _P, _I, _P, _P, _P], _I),
     "mer_laplacian_csr": ([_P, ctypes.c_int64, ctypes.c_int64, _P, _P], _I),
     "mer_precond_apply": ([_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P], _I),
     "mer_precond_solve_workspace_size": ([ctypes.c_int64], _Z),
@@ -224,6 +227,20 @@ def mer_sync_status(workspace) -> tuple[int, int]:
     tot = ctypes.c_int64(0)
     code = lib().mer_sync_status(_ptr(workspace), ctypes.byref(tot), _stream())
     return code, int(tot.value)
+
+
+def mer_forward_grad(vpix, tris, index, image, tangent, attr, tex, sh: MerShading, terms: int, out, status_ws=None):
+    n, V = vpix.shape[0], vpix.shape[1]
+    H, W = index.shape[1], index.shape[2]
+    _check(lib().mer_forward_grad(_ptr(vpix), V, _ptr(tris), tris.shape[0], n, H, W, _ptr(index), _ptr(image),
+                                  _ptr(tangent), _ptr(attr), _ptr(tex), ctypes.byref(sh), terms, _ptr(out),
+                                  _ptr(status_ws), _stream()), "mer_forward_grad")
+
+
+def mer_project_jvp(tangent_world, cams, vpix, out):
+    n, V = vpix.shape[0], vpix.shape[1]
+    _check(lib().mer_project_jvp(_ptr(tangent_world), V, _ptr(cams), n, _ptr(vpix), _ptr(out), _stream()),
+           "mer_project_jvp")
 
 
 def mer_laplacian_csr(tris: np.ndarray, V: int) -> tuple[np.ndarray, np.ndarray]:

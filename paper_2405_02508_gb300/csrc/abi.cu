@@ -25,6 +25,10 @@ extern "C" int mer_launch_batch_rasterize(const mer_vertex*, const int*, const m
 extern "C" int mer_launch_batch_render(const mer_vertex*, const int*, const mer_item*, int, long long, long long, int,
                                        void*, size_t, int*, float*, float*, const float*, const float*, const float*,
                                        const mer_shading*, float*, int, cudaStream_t);
+extern "C" int mer_launch_forward_grad(const mer_vertex*, int, const int*, int, int, int, int, const int*, const float*,
+                                       const float*, const float*, const float*, const mer_shading*, int, float*, void*,
+                                       cudaStream_t);
+extern "C" int mer_launch_project_jvp(const float*, int, const mer_camera*, int, const mer_vertex*, float*, cudaStream_t);
 extern "C" int mer_launch_project_batch(const float*, const mer_camera*, const mer_item*, int, long long, mer_vertex*,
                                         cudaStream_t);
 extern "C" int mer_launch_project_backward_batch(const mer_camera*, const mer_item*, int, long long, const mer_vertex*,
@@ -143,6 +147,30 @@ int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int 
     if (status_ws && !aligned256(status_ws)) return MER_EINVAL;
     return mer_launch_backward(vpix, V, tris, T, n, H, W, index, image, grad_image, attr, tex, sh, terms, grad_vpix,
                                grad_attr, status_ws, S(stream));
+}
+
+int mer_forward_grad(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
+                     const int32_t* index, const float* image, const float* tangent, const float* attr,
+                     const float* tex, const mer_shading* sh, int terms, float* out, void* status_ws, void* stream) {
+    if (V < 0 || T < 0 || !dims_ok(n, H, W) || !shading_ok(sh)) return MER_EINVAL;
+    if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT)) return MER_EINVAL;
+    if ((long long)n * H * W == 0) return MER_OK;
+    if (!index || !out || (V > 0 && !tangent)) return MER_EINVAL;
+    if (T > 0 && (!tris || !vpix)) return MER_EINVAL;
+    if ((terms & MER_EDGE) && !image) return MER_EINVAL;
+    if ((terms & MER_INTERIOR) && sh->n_main > 0 && !attr) return MER_EINVAL;
+    if ((terms & MER_INTERIOR) && sh->uv_offset >= 0 && !tex) return MER_EINVAL;
+    if (status_ws && !aligned256(status_ws)) return MER_EINVAL;
+    return mer_launch_forward_grad(vpix, V, tris, T, n, H, W, index, image, tangent, attr, tex, sh, terms, out,
+                                   status_ws, S(stream));
+}
+
+int mer_project_jvp(const float* tangent_world, int V, const mer_camera* cams, int n, const mer_vertex* vpix,
+                    float* tangent_vpix, void* stream) {
+    if (V < 0 || n < 0) return MER_EINVAL;
+    if ((long long)V * n == 0) return MER_OK;
+    if (!tangent_world || !cams || !vpix || !tangent_vpix) return MER_EINVAL;
+    return mer_launch_project_jvp(tangent_world, V, cams, n, vpix, tangent_vpix, S(stream));
 }
 
 int mer_edge_grad_backward(const float* image, const float* grad_image, int C, const int32_t* index,

@@ -87,6 +87,17 @@ class Renderer:
         B.mer_project_backward(cams, self.vpix, self.grad_vpix, self.grad_verts)
         return self.grad_verts
 
+    # -- forward gradients ---------------------------------------------------------------------------
+    def forward_grad(self, tangent_world: torch.Tensor, cams: torch.Tensor, attr: torch.Tensor, tex=None,
+                     terms: int = B.MER_EDGE | B.MER_INTERIOR | B.MER_INTERSECT) -> torch.Tensor:
+        """d(image)/d(theta) [n,H,W,C] for a world-space vertex tangent [V,3] (after ``forward``)."""
+        tv = torch.empty((self.n, self.V, 3), dtype=torch.float32, device=self.device)
+        B.mer_project_jvp(tangent_world.contiguous(), cams, self.vpix, tv)
+        out = torch.empty_like(self.image)
+        B.mer_forward_grad(self.vpix, self.tris, self.index, self.image, tv, attr.contiguous(), tex, self.sh, terms,
+                           out, self.workspace)
+        return out
+
     def check_status(self):
         code, _ = B.mer_sync_status(self.workspace)
         if code != B.MER_OK:
