@@ -440,7 +440,47 @@ int orc_shade(const double* scr, const int64_t* snap, const int32_t* tris, const
  * [3] intersection, [4] intersection skipped (parallel slice normals),
  * [5] intersection skipped because intersections are disabled.
  * ------------------------------------------------------------------------ */
-enum { ORC_EDGE = 1, ORC_INTERIOR = 2, ORC_INTERSECT = 4 };
+enum { ORC_EDGE = 1, ORC_INTERIOR = 2, ORC_INTERSECT = 4, ORC_EXACT_CROSSING = 8 };
+
+/* Exact-crossing gather weights for an overhang pair (an option; the default gathers with lambda at the
+ * foreground pixel centre).  The micro-edge of the pair is where the foreground triangle's outline crosses
+ * the segment from the foreground pixel centre F to the other centre O.  That crossing lies on the edge
+ * through which the segment leaves the triangle: among the edges with O on or beyond them (s E(O) <= 0 with
+ * s the area sign), the one reached first, i.e. the smallest t_k = e_k(F) / (e_k(F) - e_k(O)), compared
+ * exactly in integer arithmetic on the snapped coordinates (ties: lower k).  Along the pair axis the crossing
+ * moves with the edge's endpoints v_j, v_l (j = k+1, l = k+2) with weights 1 - u and u, where
+ * u = (F_o - v_j,o) / (v_l,o - v_j,o) is its position along the edge measured on the other axis o (unsnapped,
+ * clamped to [0, 1]; 1/2 for an edge parallel to the pair axis).  Returns 0 when no edge qualifies. */
+static int crossing_weights(const double* scr, const int64_t* snap, const int32_t* tri, int fx, int fy, int ox,
+                            int oy, int axis, int vout[2], double wout[2])
+{
+    int64_t X[3], Y[3];
+    for (int i = 0; i < 3; ++i) { X[i] = snap[2 * tri[i]]; Y[i] = snap[2 * tri[i] + 1]; }
+    int64_t a2 = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
+    if (a2 == 0) return 0;
+    int64_t sg = a2 > 0 ? 1 : -1;
+    int64_t Fx = 256 * (int64_t)fx + 128, Fy = 256 * (int64_t)fy + 128;
+    int64_t Ox = 256 * (int64_t)ox + 128, Oy = 256 * (int64_t)oy + 128;
+    int best = -1;
+    int64_t bnum = 0, bden = 1;
+    for (int k = 0; k < 3; ++k) {
+        int j = (k + 1) % 3, l = (k + 2) % 3;
+        int64_t eF = sg * edge_fn(X[j], Y[j], X[l], Y[l], Fx, Fy);
+        int64_t eO = sg * edge_fn(X[j], Y[j], X[l], Y[l], Ox, Oy);
+        if (eO > 0 || eF - eO <= 0) continue;
+        if (best < 0 || (__int128)eF * bden < (__int128)bnum * (eF - eO)) { best = k; bnum = eF; bden = eF - eO; }
+    }
+    if (best < 0) return 0;
+    int j = (best + 1) % 3, l = (best + 2) % 3;
+    int o = 1 - axis;
+    double Fo = (o == 0 ? fx : fy) + 0.5;
+    double vj = scr[3 * tri[j] + o], vl = scr[3 * tri[l] + o];
+    double u = vl != vj ? (Fo - vj) / (vl - vj) : 0.5;
+    u = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+    vout[0] = tri[j]; vout[1] = tri[l];
+    wout[0] = 1.0 - u; wout[1] = u;
+    return 1;
+}
 
 static void tri_normal(const double* scr, const int32_t* tri, double N[3])
 {
@@ -616,6 +656,19 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                 double g[3] = {0, 0, 0}, m[3] = {0, 0, 0};
                 g[axis] = dLdp;
                 m[axis] = dLdp_mag;
+                if (mode & ORC_EXACT_CROSSING) {
+                    int vv[2];
+                    double ww[2];
+                    int ok = fg == 0 ? crossing_weights(scr, snap, tris + 3 * (size_t)ta, xa, ya, xb, yb, axis, vv, ww)
+                                     : crossing_weights(scr, snap, tris + 3 * (size_t)tb, xb, yb, xa, ya, axis, vv, ww);
+                    if (ok) {
+                        for (int e = 0; e < 2; ++e) {
+                            grad_scr[3 * (size_t)vv[e] + axis] += ww[e] * dLdp;
+                            if (grad_abs) grad_abs[3 * (size_t)vv[e] + axis] += ww[e] * dLdp_mag;
+                        }
+                        continue;
+                    }
+                }
                 if (fg == 0) gather(scr, tris, ta, xa, ya, g, grad_scr, m, grad_abs);
                 else gather(scr, tris, tb, xb, yb, g, grad_scr, m, grad_abs);
             }
@@ -805,11 +858,23 @@ int orc_forward_grad(const double* scr, const int64_t* snap, const int32_t* flag
                     }
                 }
                 if (fg >= 0) {
-                    double dr[3], dr_abs[3];
-                    if (fg == 0) frag_tangent(scr, tris, ta, xa, ya, tangent, dr, dr_abs);
-                    else frag_tangent(scr, tris, tb, xb, yb, tangent, dr, dr_abs);
-                    dpdt = dr[axis];
-                    dpdt_abs = dr_abs[axis];
+                    int vv[2];
+                    double ww[2];
+                    int ok = 0;
+                    if (mode & ORC_EXACT_CROSSING)
+                        ok = fg == 0 ? crossing_weights(scr, snap, tris + 3 * (size_t)ta, xa, ya, xb, yb, axis, vv, ww)
+                                     : crossing_weights(scr, snap, tris + 3 * (size_t)tb, xb, yb, xa, ya, axis, vv, ww);
+                    if (ok) {
+                        dpdt = ww[0] * tangent[3 * (size_t)vv[0] + axis] + ww[1] * tangent[3 * (size_t)vv[1] + axis];
+                        dpdt_abs = fabs(ww[0] * tangent[3 * (size_t)vv[0] + axis]) +
+                                   fabs(ww[1] * tangent[3 * (size_t)vv[1] + axis]);
+                    } else {
+                        double dr[3], dr_abs[3];
+                        if (fg == 0) frag_tangent(scr, tris, ta, xa, ya, tangent, dr, dr_abs);
+                        else frag_tangent(scr, tris, tb, xb, yb, tangent, dr, dr_abs);
+                        dpdt = dr[axis];
+                        dpdt_abs = dr_abs[axis];
+                    }
                 }
                 for (int c = 0; c < C; ++c) {
                     const double h = 0.5 * (image[pa * C + c] - image[pb * C + c]);

@@ -29,7 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-EDGE, INTERIOR, INTERSECT = 1, 2, 4
+EDGE, INTERIOR, INTERSECT, EXACT_CROSSING = 1, 2, 4, 8
 VALID = 3
 
 

@@ -83,3 +83,21 @@ def test_project_jvp_matches_finite_differences_and_transpose(orc):
         g = rng.standard_normal((200, 3))
         gw = orc.project_backward(verts, cam, g)
         assert float((g * ts).sum()) == pytest.approx(float((gw * tw).sum()), rel=1e-12)
+
+
+@pytest.mark.parametrize("name", ["tiny", "two_spheres", "open_sphere"])
+def test_forward_grad_exact_crossing_is_transpose(orc, name):
+    """The exact-crossing option keeps forward and backward transposes of each other."""
+    sc = _small(name)
+    r = orc.render(sc)[0]
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal((sc.H, sc.W, sc.shading.C)).astype(np.float32)
+    t = rng.standard_normal((len(sc.verts), 3))
+    mode = ALL | 8
+    gs, _, _ = orc.backward(r.scr, r.snap, r.flags, sc.tris, r.index, r.image, g, sc.attr, sc.shading, mode=mode)
+    jv, mag = orc.forward_grad(r.scr, r.snap, r.flags, sc.tris, r.index, r.image, t, sc.attr, sc.shading,
+                               mode=mode, want_abs=True)
+    lhs, rhs = float((g.astype(np.float64) * jv).sum()), float((gs * t).sum())
+    assert abs(lhs - rhs) <= 1e-12 * float((np.abs(g) * mag).sum())
+    gs0, _, _ = orc.backward(r.scr, r.snap, r.flags, sc.tris, r.index, r.image, g, sc.attr, sc.shading, mode=ALL)
+    assert np.abs(gs - gs0).max() > 0  # the option changes the result

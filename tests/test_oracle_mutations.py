@@ -33,6 +33,9 @@ MUTATIONS = {
                           "const double h = 1.0 * (image[pa * C + c] - image[pb * C + c]);"),
     "forward_grad_axis": ("dpdt = dr[axis];", "dpdt = dr[1 - axis];"),
     "project_jvp_depth": ("o[2] = -dZ * iz * iz;", "o[2] = dZ * iz * iz;"),
+    "crossing_weight_order": ("wout[0] = 1.0 - u; wout[1] = u;", "wout[0] = u; wout[1] = 1.0 - u;"),
+    "crossing_first_edge": ("(__int128)eF * bden < (__int128)bnum * (eF - eO)",
+                            "(__int128)eF * bden > (__int128)bnum * (eF - eO)"),
     "project_backward_transpose": ("grad_verts[3 * v + 0] += R[0] * gX + R[3] * gY + R[6] * gZ;",
                                    "grad_verts[3 * v + 0] += R[0] * gX + R[1] * gY + R[2] * gZ;"),
 }
