@@ -98,7 +98,11 @@ typedef struct mer_shading {
 enum {
     MER_EDGE = 1,      /* micro-edge term (Eq. 11, Sec. 4.3, Eq. 12) */
     MER_INTERIOR = 2,  /* interior term Omega through barycentrics/interpolation/texture */
-    MER_INTERSECT = 4  /* scatter at geometry intersections (Eq. 12); off = the paper's ablation */
+    MER_INTERSECT = 4, /* scatter at geometry intersections (Eq. 12); off = the paper's ablation */
+    MER_EXACT_CROSSING = 8 /* option: an overhang pair's gradient goes to the two endpoints of the edge
+                              through which the segment between the pixel centres leaves the foreground
+                              triangle, weighted by the crossing's position along it (pair axis only),
+                              instead of the foreground fragment's barycentrics */
 };
 
 const char* mer_strerror(int code);

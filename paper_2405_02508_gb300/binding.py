@@ -16,7 +16,7 @@ import torch
 from . import build as _build
 
 MER_OK, MER_EINVAL, MER_ECUDA, MER_EOVERFLOW, MER_ERANGE = 0, 1, 2, 3, 4
-MER_EDGE, MER_INTERIOR, MER_INTERSECT = 1, 2, 4
+MER_EDGE, MER_INTERIOR, MER_INTERSECT, MER_EXACT_CROSSING = 1, 2, 4, 8
 CAMERA_DOUBLES = 17   # mer_camera: R[9], t[3], fx, fy, cx, cy, znear
 VERTEX_FLOATS = 8     # mer_vertex: 32 bytes
 

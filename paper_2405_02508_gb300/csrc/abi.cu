@@ -136,7 +136,7 @@ int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int 
                  const float* image, const float* grad_image, const float* attr, const float* tex,
                  const mer_shading* sh, int terms, double* grad_vpix, float* grad_attr, void* status_ws, void* stream) {
     if (V < 0 || T < 0 || !dims_ok(n, H, W) || !shading_ok(sh)) return MER_EINVAL;
-    if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT)) return MER_EINVAL;
+    if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT | MER_EXACT_CROSSING)) return MER_EINVAL;
     if ((long long)n * H * W == 0 || terms == 0) return MER_OK;
     if (!index || !grad_image || (V > 0 && !grad_vpix)) return MER_EINVAL;
     if (T > 0 && (!tris || !vpix)) return MER_EINVAL;
@@ -153,7 +153,7 @@ int mer_forward_grad(const mer_vertex* vpix, int V, const int32_t* tris, int T, 
                      const int32_t* index, const float* image, const float* tangent, const float* attr,
                      const float* tex, const mer_shading* sh, int terms, float* out, void* status_ws, void* stream) {
     if (V < 0 || T < 0 || !dims_ok(n, H, W) || !shading_ok(sh)) return MER_EINVAL;
-    if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT)) return MER_EINVAL;
+    if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT | MER_EXACT_CROSSING)) return MER_EINVAL;
     if ((long long)n * H * W == 0) return MER_OK;
     if (!index || !out || (V > 0 && !tangent)) return MER_EINVAL;
     if (T > 0 && (!tris || !vpix)) return MER_EINVAL;
@@ -294,7 +294,7 @@ int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_it
                        const float* tex, const mer_shading* sh, int terms, double* grad_vpix, float* grad_attr,
                        void* workspace, int persistent_ctas, void* stream) {
     if (!totals_ok(t, items) || !shading_ok(sh)) return MER_EINVAL;
-    if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT)) return MER_EINVAL;
+    if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT | MER_EXACT_CROSSING)) return MER_EINVAL;
     if (t->pixels == 0 || terms == 0) return MER_OK;
     if (!index || !grad_image || (t->vrecs > 0 && !grad_vpix) || (t->trecs > 0 && (!tris || !vpix))) return MER_EINVAL;
     if ((terms & MER_EDGE) && !image) return MER_EINVAL;

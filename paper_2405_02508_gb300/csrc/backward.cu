@@ -99,6 +99,7 @@ struct BwdShared {
     float sval[kSlots][3];
     float sattr[kSlots][kMaxA];
     float efrag[kTH][32][3];  // per warp: edge-term fragment gradients returned to the pixel's lane
+    float evert[kTH][32][3][2];  // exact-crossing option: per pixel, (x, y) gradients of its triangle's 3 vertices
 };
 
 // Edge term of the warp's row (all 32 lanes call it together).  Lane l owns the fragment of pixel (x0 + l, y)
@@ -106,7 +107,7 @@ struct BwdShared {
 // compacted into one list per warp and classified 32 at a time, every lane busy, the source pixel's triangle
 // taken from its lane by shuffle; a pair that scatters to the source fragment adds into that pixel's slot of a
 // per-warp shared buffer, which the owning lane finally adds to (fx, fy, fz).
-__device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, BwdShared& S, void* ws, int row,
+__device__ __forceinline__ bool edge_term(const BItem& it, const BwdArgs& a, BwdShared& S, void* ws, int row,
                                           int lane, int x, int y, int t, const int vid[3], const int X[3],
                                           const int Y[3], float& fx, float& fy, float& fz) {
     const unsigned full = 0xffffffffu;
@@ -120,11 +121,17 @@ __device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, Bwd
         m[d] = __ballot_sync(full, t >= 0 && tq != t && tq != -2);
     }
     const int n0 = __popc(m[0]), n1 = n0 + __popc(m[1]), n2 = n1 + __popc(m[2]), n = n2 + __popc(m[3]);
-    if (n == 0) return;
+    if (n == 0) return false;
     float* acc = &S.efrag[row][0][0];
     acc[3 * lane] = 0.f;
     acc[3 * lane + 1] = 0.f;
     acc[3 * lane + 2] = 0.f;
+    const bool exact = (a.terms & MER_EXACT_CROSSING) != 0;
+    float* ev = &S.evert[row][0][0][0];
+    if (exact) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ev[6 * lane + k] = 0.f;
+    }
     __syncwarp();
     const int x0 = x - lane;
     const mer_vertex* vb = it.vb;
@@ -203,6 +210,20 @@ __device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, Bwd
         }
         float ex = 0.f, ey = 0.f, ez = 0.f;
         if (!inter) {
+            if (exact) {
+                // exact-crossing option: the crossing moves with the endpoints of p's exit edge
+                const int k = exit_edge(Xs, Ys, 256 * px + 128, 256 * y + 128, 256 * qx + 128, 256 * qy + 128);
+                if (k >= 0) {
+                    const int j = (k + 1) % 3, l = (k + 2) % 3;
+                    const float4 rj = __ldg(reinterpret_cast<const float4*>(vb + vs[j]));
+                    const float4 rl = __ldg(reinterpret_cast<const float4*>(vb + vs[l]));
+                    const float u = axis == 0 ? crossing_u(Ys[j], rj.w, Ys[l], rl.w, 256 * y + 128)
+                                              : crossing_u(Xs[j], rj.z, Xs[l], rl.z, 256 * px + 128);
+                    atomicAdd(ev + 6 * src + 2 * j + axis, (1.0f - u) * dLdp);
+                    atomicAdd(ev + 6 * src + 2 * l + axis, u * dLdp);
+                    continue;
+                }
+            }
             if (axis == 0) ex = dLdp; else ey = dLdp;
         } else {
             // Eq. 12: p's triangle varies (v), q's triangle is fixed (f), slice (axis, zeta)
@@ -229,6 +250,7 @@ __device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, Bwd
     fx += acc[3 * lane];
     fy += acc[3 * lane + 1];
     fz += acc[3 * lane + 2];
+    return exact;
 }
 
 // A tile's work is split in three phases separated by CTA barriers: tile_halo (index tile + halo into shared
@@ -384,8 +406,9 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
 
     }
 
+    bool has_ev = false;
     if (a.terms & MER_EDGE) {
-        edge_term(it, a, S, ws, row, lane, x, y, t, vid, X, Y, fx, fy, fz);
+        has_ev = edge_term(it, a, S, ws, row, lane, x, y, t, vid, X, Y, fx, fy, fz);
     }
     if (t >= 0) {
 #pragma unroll
@@ -394,6 +417,13 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
             c0[k] = l * fx;
             c1[k] = l * fy;
             c2[k] = l * (fz + hz[k]);
+        }
+        if (has_ev) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                c0[k] += S.evert[row][lane][k][0];
+                c1[k] += S.evert[row][lane][k][1];
+            }
         }
     }
 

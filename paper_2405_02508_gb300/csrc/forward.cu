@@ -60,6 +60,28 @@ __device__ __forceinline__ void frag_motion(const VRec rv[3], const int vid[3], 
     }
 }
 
+// dp/dtheta of an overhang pair: the pair-axis motion of the foreground fragment (triangle rv / vid, pixel
+// (fx, fy)), or with the exact-crossing option that of the crossing on its exit edge towards pixel (ox, oy).
+__device__ __forceinline__ float overhang_rate(const VRec rv[3], const int vid[3], const float* __restrict__ tb,
+                                               int fx, int fy, int ox, int oy, int axis, bool exact) {
+    if (exact) {
+        const int X[3] = {rv[0].X, rv[1].X, rv[2].X}, Y[3] = {rv[0].Y, rv[1].Y, rv[2].Y};
+        const int k = exit_edge(X, Y, 256 * fx + 128, 256 * fy + 128, 256 * ox + 128, 256 * oy + 128);
+        if (k >= 0) {
+            const int j = (k + 1) % 3, l = (k + 2) % 3;
+            const float u = axis == 0 ? crossing_u(rv[j].Y, rv[j].ry, rv[l].Y, rv[l].ry, 256 * fy + 128)
+                                      : crossing_u(rv[j].X, rv[j].rx, rv[l].X, rv[l].rx, 256 * fx + 128);
+            float tj[3], tl[3];
+            load_tangent(tb, vid[j], tj);
+            load_tangent(tb, vid[l], tl);
+            return (1.0f - u) * tj[axis] + u * tl[axis];
+        }
+    }
+    float dr[3];
+    frag_motion(rv, vid, tb, fx, fy, dr);
+    return dr[axis];
+}
+
 __device__ __forceinline__ void plane_normal(const VRec r[3], float N[3]) {
     float p[3][3];
 #pragma unroll
@@ -186,6 +208,7 @@ __global__ void __launch_bounds__(kFTW * kFTH) k_forward_grad(const mer_vertex* 
     }
 
     if (a.terms & MER_EDGE) {
+        const bool exact = (a.terms & MER_EXACT_CROSSING) != 0;
 #pragma unroll 1
         for (int d = 0; d < 4; ++d) {
             const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
@@ -229,16 +252,13 @@ __global__ void __launch_bounds__(kFTW * kFTH) k_forward_grad(const mer_vertex* 
                     dpdt = (-nq1 / den_p) * (np0 * drp[axis] + np1 * drp[2]) +
                            (-np1 / den_q) * (nq0 * drq[axis] + nq1 * drq[2]);
                 } else {
-                    float dr[3];
-                    if (p_in_q) frag_motion(rv, vid, tb, x, y, dr);
-                    else frag_motion(rq, vq, tb, qx, qy, dr);
-                    dpdt = dr[axis];
+                    dpdt = p_in_q ? overhang_rate(rv, vid, tb, x, y, qx, qy, axis, exact)
+                                  : overhang_rate(rq, vq, tb, qx, qy, x, y, axis, exact);
                 }
             } else {
-                float dr[3];
-                if (t >= 0) frag_motion(rv, vid, tb, x, y, dr);
-                else frag_motion(rq, vq, tb, qx, qy, dr);
-                dpdt = ddx != 0 ? dr[0] : dr[1];
+                const int axis = ddx != 0 ? 0 : 1;
+                dpdt = t >= 0 ? overhang_rate(rv, vid, tb, x, y, qx, qy, axis, exact)
+                              : overhang_rate(rq, vq, tb, qx, qy, x, y, axis, exact);
             }
             // Eq. 11 transposed: both pixels of the pair change by 1/2 (I_A - I_B) dp/dtheta, A = left/top
             const size_t q = (size_t)qy * a.W + qx;

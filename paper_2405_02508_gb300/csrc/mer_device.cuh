@@ -44,6 +44,43 @@ __device__ __forceinline__ int64_t edge_fn(int xj, int yj, int xk, int yk, int p
     return (int64_t)(xj - px) * (int64_t)(yk - py) - (int64_t)(yj - py) * (int64_t)(xk - px);
 }
 
+// Exact-crossing gather option (overhang pairs): the edge k (opposite vertex k) through which the segment from
+// pixel centre F to pixel centre O (snapped units) leaves the triangle: among the edges with O on or beyond
+// them (s E_k(O) <= 0, s the area sign) the one reached first, i.e. the smallest
+// t_k = s E_k(F) / (s E_k(F) - s E_k(O)), compared exactly (128-bit products); ties go to the lower k.
+// -1 if the triangle is degenerate or no edge qualifies.
+__device__ __forceinline__ int exit_edge(const int X[3], const int Y[3], int Fx, int Fy, int Ox, int Oy) {
+    const int64_t a2 = (int64_t)(X[1] - X[0]) * (Y[2] - Y[0]) - (int64_t)(Y[1] - Y[0]) * (X[2] - X[0]);
+    if (a2 == 0) return -1;
+    const int64_t sg = a2 > 0 ? 1 : -1;
+    int best = -1;
+    int64_t bnum = 0, bden = 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int j = (k + 1) % 3, l = (k + 2) % 3;
+        const int64_t eF = sg * edge_fn(X[j], Y[j], X[l], Y[l], Fx, Fy);
+        const int64_t eO = sg * edge_fn(X[j], Y[j], X[l], Y[l], Ox, Oy);
+        if (eO > 0 || eF - eO <= 0) continue;
+        if (best < 0 || (__int128)eF * bden < (__int128)bnum * (eF - eO)) {
+            best = k;
+            bnum = eF;
+            bden = eF - eO;
+        }
+    }
+    return best;
+}
+
+// Position u in [0, 1] of the crossing along the edge v_j -> v_l, measured on the axis o orthogonal to the
+// pair axis (o = 1: y, for a horizontal pair): u = (F_o - v_j,o) / (v_l,o - v_j,o) on the unsnapped geometry
+// (v = snapped/256 + residual), differences of the integer parts taken exactly; 1/2 for an edge parallel to
+// the pair axis.  Fo_snapped = 256 * pixel + 128 on axis o.
+__device__ __forceinline__ float crossing_u(int Sj, float rj, int Sl, float rl, int Fo_snapped) {
+    const float num = (float)(Fo_snapped - Sj) * (1.0f / 256.0f) - rj;
+    const float den = (float)(Sl - Sj) * (1.0f / 256.0f) + (rl - rj);
+    float u = den != 0.0f ? num / den : 0.5f;
+    return fminf(fmaxf(u, 0.0f), 1.0f);
+}
+
 // Exact coverage of the pixel centre (px, py) (snapped units) by a raster record.
 __device__ __forceinline__ bool covers(const TriRaster& t, int px, int py, int64_t E[3]) {
     const bool neg = (t.flags & 8) != 0;

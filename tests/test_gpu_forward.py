@@ -59,15 +59,16 @@ def _gpu(sc, tangent, terms=7):
 
 
 @pytest.mark.parametrize("name", ["tiny", "two_spheres", "textured_head", "open_sphere"])
-@pytest.mark.parametrize("kind", ["translate_part", "random"])
+@pytest.mark.parametrize("kind", ["translate_part", "random", "random_exact_crossing"])
 def test_forward_grad_matches_oracle(orc, name, kind):
     sc = _scene(name)
+    terms = 7 | (8 if kind.endswith("exact_crossing") else 0)
     t = _tangent(sc, kind)
-    r, out, _, _, _ = _gpu(sc, t)
+    r, out, _, _, _ = _gpu(sc, t, terms)
     ov = orc.render(sc)[0]
     ts = orc.project_jvp(sc.verts, sc.cams[0], t)
     jv, mag = orc.forward_grad(ov.scr, ov.snap, ov.flags, sc.tris, ov.index, ov.image, ts, sc.attr, sc.shading,
-                               sc.tex, want_abs=True)
+                               sc.tex, mode=terms, want_abs=True)
     g = out[0].cpu().numpy().astype(np.float64)
     gi = r.index[0].cpu().numpy()
     # pixels whose result is not unique: depth near-ties (and their neighbours, whose pairs they enter) and
@@ -84,15 +85,16 @@ def test_forward_grad_matches_oracle(orc, name, kind):
 
 
 @pytest.mark.parametrize("name", ["two_spheres", "textured_head"])
-def test_forward_grad_is_transpose_of_device_backward(name):
+@pytest.mark.parametrize("terms", [7, 15])
+def test_forward_grad_is_transpose_of_device_backward(name, terms):
     """sum_p g_p . JVP(t)_p = sum_v grad_world(g)_v . t_v with both sides from the device kernels."""
     import torch
 
     sc = _scene(name)
     t = _tangent(sc, "random")
-    r, out, cams, attr, tex = _gpu(sc, t)
+    r, out, cams, attr, tex = _gpu(sc, t, terms)
     g = torch.from_numpy(sc.upstream()).cuda()
-    gw = r.backward(g, cams, attr, tex).double().cpu().numpy()
+    gw = r.backward(g, cams, attr, tex, terms).double().cpu().numpy()
     lhs = float((g.double() * out.double()).sum())
     rhs = float((gw * t).sum())
     scale = float((g.double().abs() * out.double().abs()).sum())

@@ -119,6 +119,15 @@ def test_parity_intersections_off(orc):
     run_parity(orc, sc, sc.upstream(), terms=1 | 2)
 
 
+@pytest.mark.parametrize("scene", ["tiny", "two_spheres", "open_sphere"])
+def test_parity_exact_crossing_option(orc, scene):
+    """The exact-crossing gather option (overhang gradients to the exit edge's endpoints) against the oracle."""
+    sc = {"tiny": lambda: scenes.tiny_icosphere(),
+          "two_spheres": lambda: scenes.two_spheres(H=256, W=256, subdiv=4),
+          "open_sphere": lambda: scenes.open_sphere(H=256, W=256)}[scene]()
+    run_parity(orc, sc, sc.upstream(), terms=ALL | 8)
+
+
 def test_parity_edge_only_and_interior_only(orc):
     sc = scenes.two_spheres(H=256, W=256, subdiv=4)
     run_parity(orc, sc, sc.upstream(), terms=1 | 4)
