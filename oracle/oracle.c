@@ -451,8 +451,8 @@ enum { ORC_EDGE = 1, ORC_INTERIOR = 2, ORC_INTERSECT = 4, ORC_EXACT_CROSSING = 8
  * moves with the edge's endpoints v_j, v_l (j = k+1, l = k+2) with weights 1 - u and u, where
  * u = (F_o - v_j,o) / (v_l,o - v_j,o) is its position along the edge measured on the other axis o (unsnapped,
  * clamped to [0, 1]; 1/2 for an edge parallel to the pair axis).  Returns 0 when no edge qualifies. */
-static int crossing_weights(const double* scr, const int64_t* snap, const int32_t* tri, int fx, int fy, int ox,
-                            int oy, int axis, int vout[2], double wout[2])
+int orc_crossing_weights(const double* scr, const int64_t* snap, const int32_t* tri, int fx, int fy, int ox,
+                         int oy, int axis, int vout[2], double wout[2])
 {
     int64_t X[3], Y[3];
     for (int i = 0; i < 3; ++i) { X[i] = snap[2 * tri[i]]; Y[i] = snap[2 * tri[i] + 1]; }
@@ -659,8 +659,8 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
                 if (mode & ORC_EXACT_CROSSING) {
                     int vv[2];
                     double ww[2];
-                    int ok = fg == 0 ? crossing_weights(scr, snap, tris + 3 * (size_t)ta, xa, ya, xb, yb, axis, vv, ww)
-                                     : crossing_weights(scr, snap, tris + 3 * (size_t)tb, xb, yb, xa, ya, axis, vv, ww);
+                    int ok = fg == 0 ? orc_crossing_weights(scr, snap, tris + 3 * (size_t)ta, xa, ya, xb, yb, axis, vv, ww)
+                                     : orc_crossing_weights(scr, snap, tris + 3 * (size_t)tb, xb, yb, xa, ya, axis, vv, ww);
                     if (ok) {
                         for (int e = 0; e < 2; ++e) {
                             grad_scr[3 * (size_t)vv[e] + axis] += ww[e] * dLdp;
@@ -862,8 +862,8 @@ int orc_forward_grad(const double* scr, const int64_t* snap, const int32_t* flag
                     double ww[2];
                     int ok = 0;
                     if (mode & ORC_EXACT_CROSSING)
-                        ok = fg == 0 ? crossing_weights(scr, snap, tris + 3 * (size_t)ta, xa, ya, xb, yb, axis, vv, ww)
-                                     : crossing_weights(scr, snap, tris + 3 * (size_t)tb, xb, yb, xa, ya, axis, vv, ww);
+                        ok = fg == 0 ? orc_crossing_weights(scr, snap, tris + 3 * (size_t)ta, xa, ya, xb, yb, axis, vv, ww)
+                                     : orc_crossing_weights(scr, snap, tris + 3 * (size_t)tb, xb, yb, xa, ya, axis, vv, ww);
                     if (ok) {
                         dpdt = ww[0] * tangent[3 * (size_t)vv[0] + axis] + ww[1] * tangent[3 * (size_t)vv[1] + axis];
                         dpdt_abs = fabs(ww[0] * tangent[3 * (size_t)vv[0] + axis]) +

@@ -88,6 +88,8 @@ def lib():
         L.orc_project_backward.restype = None
         L.orc_forward_grad.argtypes = [P, P, P, i, P, P, i, i, P, P, P, ctypes.POINTER(OrcShading), i, P, P, P]
         L.orc_forward_grad.restype = i
+        L.orc_crossing_weights.argtypes = [P, P, P, i, i, i, i, i, P, P]
+        L.orc_crossing_weights.restype = i
         L.orc_project_jvp.argtypes = [P, i, ctypes.POINTER(OrcCamera), P, P]
         L.orc_project_jvp.restype = None
         _lib = L
@@ -251,6 +253,18 @@ def forward_grad(scr, snap, flags, tris, index, image, tangent, attr, sh, tex=No
                                 _p(mag))
     assert rc == 0
     return (out, mag) if want_abs else out
+
+
+def crossing_weights(scr, snap, tri, f, o, axis):
+    """Exact-crossing weights of one overhang pair: foreground pixel f = (x, y), other pixel o; ->
+    (vertex ids [2], weights [2]) or None."""
+    v = np.zeros(2, np.int32)
+    w = np.zeros(2)
+    ok = lib().orc_crossing_weights(_p(np.ascontiguousarray(scr, dtype=np.float64)),
+                                    _p(np.ascontiguousarray(snap, dtype=np.int64)),
+                                    _p(np.ascontiguousarray(tri, dtype=np.int32)), f[0], f[1], o[0], o[1], axis,
+                                    _p(v), _p(w))
+    return (v, w) if ok else None
 
 
 def project_jvp(verts, cam, tangent_world):

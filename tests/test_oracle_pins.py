@@ -719,3 +719,63 @@ def test_exact_crossing_closed_form_converges_fast(orc):
             err[mode] = np.linalg.norm(gs[:, :2] - ref) / np.linalg.norm(ref)
         assert err[ALL | EXACT_CROSSING] < 0.01
         assert err[ALL | EXACT_CROSSING] < err[ALL] / 10
+
+
+def _exit_point(P2, F, O):
+    """Brute force: the point where the segment F -> O leaves triangle P2 (continuous geometry), by bisection
+    on an FP64 point-in-triangle test."""
+    def cross2(a, b):
+        return a[0] * b[1] - a[1] * b[0]
+
+    def inside(q):
+        s = [cross2(P2[(i + 1) % 3] - P2[i], q - P2[i]) for i in range(3)]
+        return all(v >= 0 for v in s) or all(v <= 0 for v in s)
+    lo, hi = 0.0, 1.0
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if inside(F + mid * (O - F)):
+            lo = mid
+        else:
+            hi = mid
+    return F + lo * (O - F)
+
+
+def test_exact_crossing_weights_equal_brute_force_derivatives(orc):
+    """For every overhang pair of random triangles, the exact-crossing weights equal the derivatives of the
+    brute-force exit point's pair-axis coordinate with respect to each vertex's pair-axis coordinate (central
+    differences of a bisection), away from vertices and from points the snapping could move."""
+    rng = np.random.default_rng(31)
+    checked = 0
+    for trial in range(25):
+        P2 = rng.uniform(2.0, 30.0, (3, 2))
+        scr, snap, flags = orc.snap_screen(np.concatenate([P2, np.full((3, 1), 0.5)], axis=1))
+        tri = np.array([0, 1, 2], np.int32)
+        P2 = scr[:, :2]
+        for y in range(32):
+            for x in range(32):
+                if not orc.covers_pixel(snap, flags, tri[None], 0, x, y):
+                    continue
+                for axis, (dx, dy) in ((0, (1, 0)), (0, (-1, 0)), (1, (0, 1)), (1, (0, -1))):
+                    ox, oy = x + dx, y + dy
+                    if orc.covers_pixel(snap, flags, tri[None], 0, ox, oy):
+                        continue
+                    F = np.array([x + 0.5, y + 0.5])
+                    O = np.array([ox + 0.5, oy + 0.5])
+                    c = _exit_point(P2, F, O)
+                    if np.min(np.linalg.norm(P2 - c, axis=1)) < 1e-2:
+                        continue  # at a corner: the exit edge is not unique
+                    if np.linalg.norm(c - F) < 1e-3 or np.linalg.norm(c - O) < 1e-3:
+                        continue  # a centre on the outline: snapping decides
+                    res = orc.crossing_weights(scr, snap, tri, (x, y), (ox, oy), axis)
+                    assert res is not None
+                    w = np.zeros(3)
+                    w[res[0]] = res[1]
+                    h = 1e-6
+                    for k in range(3):
+                        Pp, Pm = P2.copy(), P2.copy()
+                        Pp[k, axis] += h
+                        Pm[k, axis] -= h
+                        fd = (_exit_point(Pp, F, O)[axis] - _exit_point(Pm, F, O)[axis]) / (2 * h)
+                        assert fd == pytest.approx(w[k], abs=1e-5), (trial, x, y, axis, k, fd, w)
+                    checked += 1
+    assert checked > 200
