@@ -146,8 +146,8 @@ int mer_rasterize(const mer_vertex* vpix, int V, const int32_t* tris, int T, int
  *
  * The workspace is a 64 MiB array in the library's own device memory (a file-scope __device__ array:
  * every GPU that loads the library holds it until the process exits).  The call rejects, with
- * MER_EINVAL, sizes whose fixed workspace part does not fit in it: 256 B of header, 12 B per bin tile
- * (n * ceil(H/tile) * ceil(W/tile) tiles), 48 B per (view, triangle); the rest holds the bin lists.
+ * MER_EINVAL, sizes whose fixed workspace part does not fit in it: 256 B of header, 16 B per bin tile
+ * (n * ceil(H/tile) * ceil(W/tile) tiles), 64 B per (view, triangle); the rest holds the bin lists.
  * When the bin lists do not fit, the results are not valid and *status (device int, or NULL) receives
  * bit 0 (bit 1: a triangle index >= V).  *status is written on `stream` after the raster; read it once
  * the stream has passed that point.

@@ -30,14 +30,16 @@ static_assert(sizeof(WsHeader) == 256, "header");
 constexpr int kStatusOverflow = 1;
 constexpr int kStatusRange = 2;
 
-// Per (view, triangle) raster record written by the binning pass, 48 bytes.
+// Per (view, triangle) raster record written by the binning pass, 64 bytes.
 struct TriRaster {
     int X[3], Y[3];   // snapped vertex positions
     float zd[3];      // zeta_i / |E_0 + E_1 + E_2|, FP32
     int flags;        // bits 0..2: edge i is top-left; bit 3: negative area; bit 4: small (32-bit path); bit 31: culled
     short bx0, bx1, by0, by1;  // inclusive pixel bounding box of the covered centres
+    float zmax;       // largest vertex zeta: no fragment of the triangle has a larger depth key
+    int pad[3];
 };
-static_assert(sizeof(TriRaster) == 48, "TriRaster");
+static_assert(sizeof(TriRaster) == 64, "TriRaster");
 
 __device__ __forceinline__ int64_t edge_fn(int xj, int yj, int xk, int yk, int px, int py) {
     // cross(v_j - P, v_k - P); every factor fits int32 (|X| <= 2^29, P < 2^22)

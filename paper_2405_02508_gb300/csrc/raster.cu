@@ -99,6 +99,7 @@ __device__ __forceinline__ void setup_count_one(const RItem& it, int t, int tile
     const float Df = ll2f_rn(a2 < 0 ? -a2 : a2);
 #pragma unroll
     for (int k = 0; k < 3; ++k) r.zd[k] = __fdiv_rn(v[k].zeta, Df);
+    r.zmax = fmaxf(v[0].zeta, fmaxf(v[1].zeta, v[2].zeta));
     r.bx0 = (short)x0; r.bx1 = (short)x1; r.by0 = (short)y0; r.by1 = (short)y1;
     it.recs[t] = r;
     int* cnt = counts + it.tile0;
@@ -106,14 +107,20 @@ __device__ __forceinline__ void setup_count_one(const RItem& it, int t, int tile
         for (int tx = x0 / tile; tx <= x1 / tile; ++tx) atomicAdd(cnt + ty * it.ntx + tx, 1);
 }
 
+// Bin lists are split by facing: triangles with a negative snapped area (facing the camera for an
+// outward-oriented mesh) from the start of the tile's list, the others from its end.  The raster draws the
+// first part, then culls triangles of the second part that lie wholly behind the tile's depth buffer.
 __device__ __forceinline__ void fill_one(const RItem& it, int t, int tile, const int* __restrict__ offs,
-                                         int* __restrict__ cursor, int* __restrict__ list, long long capacity) {
+                                         const int* __restrict__ counts, int* __restrict__ cursor,
+                                         int* __restrict__ cursor_back, int* __restrict__ list, long long capacity) {
     const TriRaster& r = it.recs[t];
     if (r.flags < 0) return;
+    const bool front = (r.flags & 8) != 0;
     for (int ty = r.by0 / tile; ty <= r.by1 / tile; ++ty)
         for (int tx = r.bx0 / tile; tx <= r.bx1 / tile; ++tx) {
             const size_t g = it.tile0 + (size_t)ty * it.ntx + tx;
-            const long long pos = (long long)offs[g] + atomicAdd(cursor + g, 1);
+            const long long pos = front ? (long long)offs[g] + atomicAdd(cursor + g, 1)
+                                        : (long long)offs[g] + counts[g] - 1 - atomicAdd(cursor_back + g, 1);
             if (pos < capacity) list[pos] = t;
         }
 }
@@ -178,11 +185,13 @@ __global__ void k_scan_sums(int* __restrict__ sums, int nb, void* ws, long long 
     }
 }
 
+// Adds the block offsets and clears the front and back fill cursors (cursor[0, 2N)).
 __global__ void k_scan_add(int* __restrict__ out, long long N, const int* __restrict__ sums, int* __restrict__ cursor) {
     const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
     if (i < N) {
         out[i] += sums[blockIdx.x];
         cursor[i] = 0;
+        cursor[N + i] = 0;
     }
 }
 
@@ -197,29 +206,64 @@ constexpr int kRasterThreads = 256;
 
 template <int TS>
 struct RasterShared {
-    TriRaster rec[kStage];
-    int id[kStage];
+    static constexpr int kStageTS = TS >= 64 ? 160 : kStage;  // keeps the 64 x 64 tile within 48 KB
+    TriRaster rec[kStageTS];
+    int id[kStageTS];
     unsigned long long zbuf[TS * TS];
+    float red[kRasterThreads / 32];
 };
+
+// Smallest depth key (zeta_test) over the tile's pixels inside the image, 0 if one of them is still empty.
+// All threads call it; it starts and ends with a barrier.
+template <int TS>
+__device__ __forceinline__ float tile_min_zeta(RasterShared<TS>& S, int ox, int oy, int W, int H) {
+    __syncthreads();
+    float mn = 3.0e38f;
+    for (int i = threadIdx.x; i < TS * TS; i += kRasterThreads) {
+        const int px = ox + (i % TS), py = oy + (i / TS);
+        if (px >= W || py >= H) continue;
+        const unsigned long long key = S.zbuf[i];
+        mn = fminf(mn, key ? __uint_as_float((unsigned)(key >> 32)) : 0.0f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    float r = S.red[0];
+#pragma unroll
+    for (int w = 1; w < kRasterThreads / 32; ++w) r = fminf(r, S.red[w]);
+    __syncthreads();
+    return r;
+}
 
 // SHADE: also shade every pixel of the tile from its z-buffer winner (shade_fragment, as the deferred
 // shading kernels do from the index image).
+// The tile's list holds the camera-facing triangles first (nfront of them) and the others after; before
+// the second part the tile's smallest depth key is taken, and a triangle of that part whose largest vertex
+// zeta (with a margin above the FP32 rounding of the key) is below it cannot win any pixel: it is skipped.
 template <int TS, bool SHADE>
 __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, const int* __restrict__ offs,
-                                            const int* __restrict__ cnts, const int* __restrict__ list,
-                                            bool overflow, RasterShared<TS>& S, int* __restrict__ index,
-                                            float* __restrict__ depth, float* __restrict__ bary,
-                                            const ShadeOut& so, void* ws) {
+                                            const int* __restrict__ cnts, const int* __restrict__ nfront,
+                                            const int* __restrict__ list, bool overflow, RasterShared<TS>& S,
+                                            int* __restrict__ index, float* __restrict__ depth,
+                                            float* __restrict__ bary, const ShadeOut& so, void* ws) {
+    constexpr int kSt = RasterShared<TS>::kStageTS;
     const long long tile = it.tile0 + local_tile;
     const int ty = local_tile / it.ntx, tx = local_tile % it.ntx;
     const int ox = tx * TS, oy = ty * TS;
     for (int i = threadIdx.x; i < TS * TS; i += kRasterThreads) S.zbuf[i] = 0ull;
     const int count = overflow ? 0 : cnts[tile];
     const int off = overflow ? 0 : offs[tile];
+    const int nf = overflow ? 0 : min(nfront[tile], count);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = kRasterThreads / 32;
-    for (int base = 0; base < count; base += kStage) {
-        const int m = min(kStage, count - base);
+    float zcull = 0.0f;
+    int m = 0;
+    for (int base = 0; base < count; base += m) {
+        // stage boundaries fall on the front / back split so each stage is one part
+        const int lim = base < nf ? nf : count;
+        m = min(kSt, lim - base);
+        if (base == nf && base > 0) zcull = tile_min_zeta<TS>(S, ox, oy, it.W, it.H);
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += kRasterThreads) {
             const int t = list[off + base + j];
@@ -227,8 +271,10 @@ __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, con
             S.id[j] = t;
         }
         __syncthreads();
+        const bool back = base >= nf;
         for (int j = warp; j < m; j += kWarps) {
             const TriRaster& r = S.rec[j];
+            if (back && r.zmax * (1.0f + 0x1p-20f) < zcull) continue;  // hidden behind the whole tile
             const int x0 = max((int)r.bx0, ox), x1 = min((int)r.bx1, ox + TS - 1);
             const int y0 = max((int)r.by0, oy), y1 = min((int)r.by1, oy + TS - 1);
             const int bw = x1 - x0 + 1, bh = y1 - y0 + 1;
@@ -325,17 +371,19 @@ __global__ void k_setup_count(const mer_vertex* __restrict__ vpix, const int* __
 }
 
 __global__ void k_bin_fill(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris, BinGeom g,
-                           TriRaster* __restrict__ recs, const int* __restrict__ offs, int* __restrict__ cursor,
-                           int* __restrict__ list, long long capacity) {
+                           TriRaster* __restrict__ recs, const int* __restrict__ offs, const int* __restrict__ counts,
+                           int* __restrict__ cursor, int* __restrict__ list, long long capacity) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)g.T * g.n) return;
     const int view = (int)(i / g.T), t = (int)(i % g.T);
-    fill_one(view_item(g, vpix, tris, recs, view), t, g.tile, offs, cursor, list, capacity);
+    fill_one(view_item(g, vpix, tris, recs, view), t, g.tile, offs, counts, cursor,
+             cursor + (long long)g.n * g.tiles_per_view, list, capacity);
 }
 
 template <int TS>
 __global__ void __launch_bounds__(kRasterThreads) k_raster(TriRaster* __restrict__ recs, BinGeom g,
                                                            const int* __restrict__ offs, const int* __restrict__ cnts,
+                                                           const int* __restrict__ nfront,
                                                            const int* __restrict__ list, const mer_vertex* __restrict__ vpix,
                                                            const int* __restrict__ tris, void* ws, long long capacity,
                                                            int* __restrict__ index, float* __restrict__ depth,
@@ -348,8 +396,8 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(TriRaster* __restrict
     const int local = (int)(tile % g.tiles_per_view);
     ShadeOut none;
     none.attr = nullptr; none.tex = nullptr; none.image = nullptr;
-    raster_tile<TS, false>(view_item(g, vpix, tris, recs, view), local, offs, cnts, list, overflow, S, index, depth,
-                           bary, none, ws);
+    raster_tile<TS, false>(view_item(g, vpix, tris, recs, view), local, offs, cnts, nfront, list, overflow, S, index,
+                           depth, bary, none, ws);
 }
 
 // ---- batched entry: items from a table ----
@@ -385,12 +433,14 @@ __global__ void k_setup_count_batch(const mer_vertex* __restrict__ vpix, const i
 
 __global__ void k_bin_fill_batch(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris, BatchGeom b,
                                  TriRaster* __restrict__ recs, const int* __restrict__ offs,
-                                 int* __restrict__ cursor, int* __restrict__ list, long long capacity) {
+                                 const int* __restrict__ counts, int* __restrict__ cursor, int* __restrict__ list,
+                                 long long capacity) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.trecs) return;
     const int k = find_item(b.items, b.n_items, i, kFieldTrec);
     const mer_item m = b.items[k];
-    fill_one(batch_item(m, b.tile, vpix, tris, recs), (int)(i - m.trec), b.tile, offs, cursor, list, capacity);
+    fill_one(batch_item(m, b.tile, vpix, tris, recs), (int)(i - m.trec), b.tile, offs, counts, cursor,
+             cursor + b.tiles, list, capacity);
 }
 
 // Persistent: each CTA takes the next global tile from the work queue until none is left.
@@ -398,6 +448,7 @@ template <int TS, bool SHADE>
 __global__ void __launch_bounds__(kRasterThreads) k_raster_batch(TriRaster* __restrict__ recs, BatchGeom b,
                                                                  const int* __restrict__ offs,
                                                                  const int* __restrict__ cnts,
+                                                                 const int* __restrict__ nfront,
                                                                  const int* __restrict__ list,
                                                                  const mer_vertex* __restrict__ vpix,
                                                                  const int* __restrict__ tris, void* ws,
@@ -415,8 +466,8 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_batch(TriRaster* __re
         if (g >= b.tiles) break;
         const int k = find_item(b.items, b.n_items, g, kFieldTile);
         const mer_item m = b.items[k];
-        raster_tile<TS, SHADE>(batch_item(m, b.tile, vpix, tris, recs), (int)(g - m.tile), offs, cnts, list, overflow,
-                               S, index, depth, bary, so, ws);  // ends with a barrier: s_tile may be overwritten after it
+        raster_tile<TS, SHADE>(batch_item(m, b.tile, vpix, tris, recs), (int)(g - m.tile), offs, cnts, nfront, list,
+                               overflow, S, index, depth, bary, so, ws);  // ends with a barrier: s_tile may be overwritten after it
     }
 }
 
@@ -442,7 +493,7 @@ RasterLayout layout_for(long long ntiles, long long nrecs, long long capacity) {
     L.hdr = o; o += align256(sizeof(WsHeader));
     L.counts = o; o += align256((size_t)ntiles * 4);
     L.offs = o; o += align256((size_t)ntiles * 4);
-    L.cursor = o; o += align256((size_t)ntiles * 4);
+    L.cursor = o; o += align256((size_t)ntiles * 8);  // front and back fill cursors
     L.sums = o; o += align256((size_t)(L.nblocks + 1) * 4);
     L.recs = o; o += align256((size_t)nrecs * sizeof(TriRaster));
     L.list = o; o += align256((size_t)capacity * 4);
@@ -500,12 +551,13 @@ extern "C" int mer_launch_rasterize(const mer_vertex* vpix, int V, const int* tr
     if (NT > 0) k_setup_count<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(vpix, tris, g, recs, counts, hdr);
     launch_scan(L, base, capacity, s);
     if (NT > 0)
-        k_bin_fill<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(vpix, tris, g, recs, offs, cursor, list, capacity);
+        k_bin_fill<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(vpix, tris, g, recs, offs, counts, cursor, list,
+                                                                capacity);
     const unsigned grid = (unsigned)L.ntiles;
     switch (tile) {
-        case 8: k_raster<8><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
-        case 16: k_raster<16><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
-        case 32: k_raster<32><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary); break;
+        case 8: k_raster<8><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, cursor, list, vpix, tris, hdr, capacity, index, depth, bary); break;
+        case 16: k_raster<16><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, cursor, list, vpix, tris, hdr, capacity, index, depth, bary); break;
+        case 32: k_raster<32><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, cursor, list, vpix, tris, hdr, capacity, index, depth, bary); break;
         default: return 1;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
@@ -517,7 +569,7 @@ extern "C" size_t mer_batch_raster_workspace_size(long long tiles, long long tre
 
 template <int TS, bool SHADE>
 static int launch_raster_batch(unsigned grid, TriRaster* recs, BatchGeom b, const int* offs, const int* counts,
-                               const int* list, const mer_vertex* vpix, const int* tris, void* hdr, long long capacity,
+                               const int* nfront, const int* list, const mer_vertex* vpix, const int* tris, void* hdr, long long capacity,
                                int* index, float* depth, float* bary, const ShadeOut& so, cudaStream_t s) {
     if (grid == 0) {
         int per_sm = 0, sms = 0, dev = 0;
@@ -528,20 +580,20 @@ static int launch_raster_batch(unsigned grid, TriRaster* recs, BatchGeom b, cons
             return 2;
         grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
     }
-    k_raster_batch<TS, SHADE><<<grid, kRasterThreads, 0, s>>>(recs, b, offs, counts, list, vpix, tris, hdr, capacity,
+    k_raster_batch<TS, SHADE><<<grid, kRasterThreads, 0, s>>>(recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity,
                                                               index, depth, bary, so);
     return 0;
 }
 
 template <bool SHADE>
 static int launch_raster_batch_tile(int tile, unsigned grid, TriRaster* recs, BatchGeom b, const int* offs,
-                                    const int* counts, const int* list, const mer_vertex* vpix, const int* tris,
+                                    const int* counts, const int* nfront, const int* list, const mer_vertex* vpix, const int* tris,
                                     void* hdr, long long capacity, int* index, float* depth, float* bary,
                                     const ShadeOut& so, cudaStream_t s) {
     switch (tile) {
-        case 16: return launch_raster_batch<16, SHADE>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
-        case 32: return launch_raster_batch<32, SHADE>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
-        case 64: return launch_raster_batch<64, SHADE>(grid, recs, b, offs, counts, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
+        case 16: return launch_raster_batch<16, SHADE>(grid, recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
+        case 32: return launch_raster_batch<32, SHADE>(grid, recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
+        case 64: return launch_raster_batch<64, SHADE>(grid, recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
         default: return 1;
     }
 }
@@ -567,15 +619,15 @@ static int batch_raster(const mer_vertex* vpix, const int* tris, const mer_item*
     if (trecs > 0) k_setup_count_batch<<<(unsigned)((trecs + 255) / 256), 256, 0, s>>>(vpix, tris, b, recs, counts, hdr);
     launch_scan(L, base, capacity, s);  // also resets the raster work queue
     if (trecs > 0)
-        k_bin_fill_batch<<<(unsigned)((trecs + 255) / 256), 256, 0, s>>>(vpix, tris, b, recs, offs, cursor, list,
+        k_bin_fill_batch<<<(unsigned)((trecs + 255) / 256), 256, 0, s>>>(vpix, tris, b, recs, offs, counts, cursor, list,
                                                                         capacity);
     if (tiles > 0) {
         const unsigned grid = persistent_ctas > 0 ? (unsigned)persistent_ctas : 0u;
         ShadeOut none;
         none.attr = nullptr; none.tex = nullptr; none.image = nullptr;
-        const int rc = so ? launch_raster_batch_tile<true>(tile, grid, recs, b, offs, counts, list, vpix, tris, hdr,
+        const int rc = so ? launch_raster_batch_tile<true>(tile, grid, recs, b, offs, counts, cursor, list, vpix, tris, hdr,
                                                            capacity, index, depth, bary, *so, s)
-                          : launch_raster_batch_tile<false>(tile, grid, recs, b, offs, counts, list, vpix, tris, hdr,
+                          : launch_raster_batch_tile<false>(tile, grid, recs, b, offs, counts, cursor, list, vpix, tris, hdr,
                                                             capacity, index, depth, bary, none, s);
         if (rc) return rc;
     }
