@@ -93,13 +93,14 @@ struct BItem {
 
 constexpr int kMaxA = 4;  // attribute-gradient channels carried through the per-tile aggregation
 
+template <bool ATTR, bool EXACT>
 struct BwdShared {
     int sidx[kHH][kHW];
     int skey[kSlots];
     float sval[kSlots][3];
-    float sattr[kSlots][kMaxA];
+    float sattr[ATTR ? kSlots : 1][kMaxA];
     float efrag[kTH][32][3];  // per warp: edge-term fragment gradients returned to the pixel's lane
-    float evert[kTH][32][3][2];  // exact-crossing option: per pixel, (x, y) gradients of its triangle's 3 vertices
+    float evert[EXACT ? kTH : 1][32][3][2];  // exact-crossing option: per pixel, (x, y) per triangle vertex
 };
 
 // Edge term of the warp's row (all 32 lanes call it together).  Lane l owns the fragment of pixel (x0 + l, y)
@@ -107,7 +108,8 @@ struct BwdShared {
 // compacted into one list per warp and classified 32 at a time, every lane busy, the source pixel's triangle
 // taken from its lane by shuffle; a pair that scatters to the source fragment adds into that pixel's slot of a
 // per-warp shared buffer, which the owning lane finally adds to (fx, fy, fz).
-__device__ __forceinline__ bool edge_term(const BItem& it, const BwdArgs& a, BwdShared& S, void* ws, int row,
+template <bool ATTR, bool EXACT>
+__device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, BwdShared<ATTR, EXACT>& S, void* ws, int row,
                                           int lane, int x, int y, int t, const int vid[3], const int X[3],
                                           const int Y[3], float& fx, float& fy, float& fz) {
     const unsigned full = 0xffffffffu;
@@ -121,16 +123,26 @@ __device__ __forceinline__ bool edge_term(const BItem& it, const BwdArgs& a, Bwd
         m[d] = __ballot_sync(full, t >= 0 && tq != t && tq != -2);
     }
     const int n0 = __popc(m[0]), n1 = n0 + __popc(m[1]), n2 = n1 + __popc(m[2]), n = n2 + __popc(m[3]);
-    if (n == 0) return false;
+    if (n == 0) {
+        if (EXACT) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                S.evert[row][lane][k][0] = 0.f;
+                S.evert[row][lane][k][1] = 0.f;
+            }
+        }
+        return;
+    }
     float* acc = &S.efrag[row][0][0];
     acc[3 * lane] = 0.f;
     acc[3 * lane + 1] = 0.f;
     acc[3 * lane + 2] = 0.f;
-    const bool exact = (a.terms & MER_EXACT_CROSSING) != 0;
-    float* ev = &S.evert[row][0][0][0];
-    if (exact) {
+    if (EXACT) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) ev[6 * lane + k] = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            S.evert[row][lane][k][0] = 0.f;
+            S.evert[row][lane][k][1] = 0.f;
+        }
     }
     __syncwarp();
     const int x0 = x - lane;
@@ -210,17 +222,17 @@ __device__ __forceinline__ bool edge_term(const BItem& it, const BwdArgs& a, Bwd
         }
         float ex = 0.f, ey = 0.f, ez = 0.f;
         if (!inter) {
-            if (exact) {
+            if (EXACT) {
                 // exact-crossing option: the crossing moves with the endpoints of p's exit edge
-                const int k = exit_edge(Xs, Ys, 256 * px + 128, 256 * y + 128, 256 * qx + 128, 256 * qy + 128);
-                if (k >= 0) {
-                    const int j = (k + 1) % 3, l = (k + 2) % 3;
+                const int e = exit_edge(Xs, Ys, 256 * px + 128, 256 * y + 128, 256 * qx + 128, 256 * qy + 128);
+                if (e >= 0) {
+                    const int j = (e + 1) % 3, l = (e + 2) % 3;
                     const float4 rj = __ldg(reinterpret_cast<const float4*>(vb + vs[j]));
                     const float4 rl = __ldg(reinterpret_cast<const float4*>(vb + vs[l]));
                     const float u = axis == 0 ? crossing_u(Ys[j], rj.w, Ys[l], rl.w, 256 * y + 128)
                                               : crossing_u(Xs[j], rj.z, Xs[l], rl.z, 256 * px + 128);
-                    atomicAdd(ev + 6 * src + 2 * j + axis, (1.0f - u) * dLdp);
-                    atomicAdd(ev + 6 * src + 2 * l + axis, u * dLdp);
+                    atomicAdd(&S.evert[row][src][j][axis], (1.0f - u) * dLdp);
+                    atomicAdd(&S.evert[row][src][l][axis], u * dLdp);
                     continue;
                 }
             }
@@ -250,7 +262,6 @@ __device__ __forceinline__ bool edge_term(const BItem& it, const BwdArgs& a, Bwd
     fx += acc[3 * lane];
     fy += acc[3 * lane + 1];
     fz += acc[3 * lane + 2];
-    return exact;
 }
 
 // A tile's work is split in three phases separated by CTA barriers: tile_halo (index tile + halo into shared
@@ -258,8 +269,8 @@ __device__ __forceinline__ bool edge_term(const BItem& it, const BwdArgs& a, Bwd
 // global memory, slots cleared for the next tile).  The table starts clear (table_clear once per CTA), and a
 // persistent CTA overlaps the flush of one tile with the halo load of the next.
 
-template <bool ATTR>
-__device__ __forceinline__ void table_clear(BwdShared& S) {
+template <bool ATTR, bool EXACT>
+__device__ __forceinline__ void table_clear(BwdShared<ATTR, EXACT>& S) {
     for (int i = threadIdx.x; i < kSlots; i += kThreads) {
         S.skey[i] = -1;
         S.sval[i][0] = 0.f;
@@ -272,7 +283,8 @@ __device__ __forceinline__ void table_clear(BwdShared& S) {
     }
 }
 
-__device__ __forceinline__ void tile_halo(const BItem& it, int tx, int ty, BwdShared& S) {
+template <bool ATTR, bool EXACT>
+__device__ __forceinline__ void tile_halo(const BItem& it, int tx, int ty, BwdShared<ATTR, EXACT>& S) {
     for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
         const int hy = i / kHW, hx = i % kHW;
         const int gx = tx * kTW + hx - 1, gy = ty * kTH + hy - 1;
@@ -283,9 +295,9 @@ __device__ __forceinline__ void tile_halo(const BItem& it, int tx, int ty, BwdSh
 // The 32x8 tile (tx, ty) of an item, after tile_halo and a barrier.
 // ATTR: also produce the attribute gradients (channels [a0, a0 + A) of each vertex's attribute row, A <= 4:
 // the interpolated channels, or (u, v) in texture mode), aggregated like the vertex gradients.
-template <bool ATTR>
+template <bool ATTR, bool EXACT>
 __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, const BwdArgs& a,
-                                             const float* __restrict__ tex, BwdShared& S, void* ws) {
+                                             const float* __restrict__ tex, BwdShared<ATTR, EXACT>& S, void* ws) {
     const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
     const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
@@ -406,9 +418,8 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
 
     }
 
-    bool has_ev = false;
     if (a.terms & MER_EDGE) {
-        has_ev = edge_term(it, a, S, ws, row, lane, x, y, t, vid, X, Y, fx, fy, fz);
+        edge_term(it, a, S, ws, row, lane, x, y, t, vid, X, Y, fx, fy, fz);
     }
     if (t >= 0) {
 #pragma unroll
@@ -418,7 +429,7 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
             c1[k] = l * fy;
             c2[k] = l * (fz + hz[k]);
         }
-        if (has_ev) {
+        if (EXACT && (a.terms & MER_EDGE)) {  // the exact-crossing parts, already split per vertex
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 c0[k] += S.evert[row][lane][k][0];
@@ -497,8 +508,8 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
 }
 
 // After tile_compute and a barrier: add the table to global memory and clear it.
-template <bool ATTR>
-__device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, BwdShared& S) {
+template <bool ATTR, bool EXACT>
+__device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, BwdShared<ATTR, EXACT>& S) {
     const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
     const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
     double* gvv = it.gv;
@@ -525,14 +536,14 @@ __device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, Bw
     }
 }
 
-template <bool ATTR>
+template <bool ATTR, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
                                                        const int* __restrict__ index, const float* __restrict__ image,
                                                        const float* __restrict__ grad, const float* __restrict__ attr,
                                                        const float* __restrict__ tex, BwdArgs a,
                                                        double* __restrict__ grad_vpix, float* __restrict__ grad_attr,
                                                        void* ws) {
-    __shared__ BwdShared S;
+    __shared__ BwdShared<ATTR, EXACT> S;
     const int tiles_per_view = a.ntx * a.nty;
     const int view = blockIdx.x / tiles_per_view;
     const int local = blockIdx.x % tiles_per_view;
@@ -547,16 +558,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __re
     it.gv = grad_vpix + (size_t)view * a.V * 3;
     it.gattr = grad_attr;
     it.V = a.V; it.T = a.T; it.H = a.H; it.W = a.W;
-    table_clear<ATTR>(S);
+    table_clear(S);
     tile_halo(it, local % a.ntx, local / a.ntx, S);
     __syncthreads();
-    tile_compute<ATTR>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
+    tile_compute<ATTR, EXACT>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
     __syncthreads();
-    tile_flush<ATTR>(it, a, S);
+    tile_flush(it, a, S);
 }
 
 // Persistent: each CTA takes the next backward tile of any item from the work queue.
-template <bool ATTR>
+template <bool ATTR, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex* __restrict__ vpix,
                                                              const int* __restrict__ tris,
                                                              const mer_item* __restrict__ items, int n_items,
@@ -567,20 +578,29 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex
                                                              const float* __restrict__ tex, BwdArgs a,
                                                              double* __restrict__ grad_vpix,
                                                              float* __restrict__ grad_attr, void* ws) {
-    __shared__ BwdShared S;
+    __shared__ BwdShared<ATTR, EXACT> S;
     __shared__ long long s_tile;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     const int C = a.sh.C, Ca = a.sh.C_attr;
-    table_clear<ATTR>(S);
+    table_clear(S);
     if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_backward, 1ull);
     __syncthreads();
     // Per tile two barriers: after the halo load (thread 0 then takes the next tile id) and before the flush
     // (the next id is visible after it).  The flush of a tile and the halo load of the next touch disjoint
     // shared memory, and the next tile's table inserts come only after its first barrier.
+    int cur = 0;                       // item of the previous tile and its tile range [lo, hi)
+    long long lo = 0, hi = 0;
     while (true) {
         const long long g = s_tile;
         if (g >= btiles) break;
-        const mer_item m = items[find_item(items, n_items, g, kFieldBtile)];
+        // consecutive tiles of a CTA mostly belong to the same item: search the table only on a change
+        if (!(g >= lo && g < hi)) {
+            cur = find_item(items, n_items, g, kFieldBtile);
+            const mer_item c = items[cur];
+            lo = c.btile;
+            hi = lo + (long long)((c.W + kTW - 1) / kTW) * ((c.H + kTH - 1) / kTH);
+        }
+        const mer_item m = items[cur];
         const int ntx = (m.W + kTW - 1) / kTW;
         const int local = (int)(g - m.btile);
         BItem it;
@@ -597,9 +617,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex
         tile_halo(it, tx, ty, S);
         __syncthreads();
         if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_backward, 1ull);
-        tile_compute<ATTR>(it, tx, ty, a, tex, S, ws);
+        tile_compute<ATTR, EXACT>(it, tx, ty, a, tex, S, ws);
         __syncthreads();
-        tile_flush<ATTR>(it, a, S);
+        tile_flush(it, a, S);
     }
 }
 
@@ -626,18 +646,21 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
         int per_sm = 0, sms = 0, dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 2;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 2;
-        const cudaError_t e = grad_attr
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_batch<true>, kThreads, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_batch<false>, kThreads, 0);
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_batch<false, false>,
+                                                                            kThreads, 0);
         if (e != cudaSuccess) return 2;
         grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
     }
-    if (grad_attr)
-        k_backward_batch<true><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, image, grad_image,
-                                                         attr, tex, a, grad_vpix, grad_attr, ws);
-    else
-        k_backward_batch<false><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, image, grad_image,
-                                                          attr, tex, a, grad_vpix, grad_attr, ws);
+    const bool exact = (terms & MER_EXACT_CROSSING) != 0;
+#define MER_BWD_BATCH(A, E)                                                                                        \
+    k_backward_batch<A, E><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, image, grad_image, \
+                                                     attr, tex, a, grad_vpix, grad_attr, ws)
+    if (grad_attr) {
+        if (exact) MER_BWD_BATCH(true, true); else MER_BWD_BATCH(true, false);
+    } else {
+        if (exact) MER_BWD_BATCH(false, true); else MER_BWD_BATCH(false, false);
+    }
+#undef MER_BWD_BATCH
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
@@ -655,11 +678,15 @@ extern "C" int mer_launch_backward(const mer_vertex* vpix, int V, const int* tri
     a.tex_vec4 = a.tex_stride == 4 && tex && (reinterpret_cast<uintptr_t>(tex) & 15u) == 0;
     const long long blocks = (long long)a.ntx * a.nty * n;
     if (blocks == 0) return 0;
-    if (grad_attr)
-        k_backward<true><<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, image, grad_image, attr, tex, a,
-                                                               grad_vpix, grad_attr, ws);
-    else
-        k_backward<false><<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, image, grad_image, attr, tex, a,
-                                                                grad_vpix, grad_attr, ws);
+    const bool exact = (terms & MER_EXACT_CROSSING) != 0;
+#define MER_BWD(A, E)                                                                                             \
+    k_backward<A, E><<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, image, grad_image, attr, tex, a,     \
+                                                           grad_vpix, grad_attr, ws)
+    if (grad_attr) {
+        if (exact) MER_BWD(true, true); else MER_BWD(true, false);
+    } else {
+        if (exact) MER_BWD(false, true); else MER_BWD(false, false);
+    }
+#undef MER_BWD
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

@@ -459,13 +459,21 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_batch(TriRaster* __re
     __shared__ long long s_tile;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     const bool overflow = hdr->total_bins > capacity;
+    int cur = 0;                       // item of the previous tile and its tile range [lo, hi)
+    long long lo = 0, hi = 0;
     while (true) {
         if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_raster, 1ull);
         __syncthreads();
         const long long g = s_tile;
         if (g >= b.tiles) break;
-        const int k = find_item(b.items, b.n_items, g, kFieldTile);
-        const mer_item m = b.items[k];
+        // consecutive tiles of a CTA mostly belong to the same item: search the table only on a change
+        if (!(g >= lo && g < hi)) {
+            cur = find_item(b.items, b.n_items, g, kFieldTile);
+            const mer_item c = b.items[cur];
+            lo = c.tile;
+            hi = lo + (long long)((c.W + TS - 1) / TS) * ((c.H + TS - 1) / TS);
+        }
+        const mer_item m = b.items[cur];
         raster_tile<TS, SHADE>(batch_item(m, b.tile, vpix, tris, recs), (int)(g - m.tile), offs, cnts, nfront, list,
                                overflow, S, index, depth, bary, so, ws);  // ends with a barrier: s_tile may be overwritten after it
     }
