@@ -296,6 +296,17 @@ int mer_forward_grad(const mer_vertex* vpix, int V, const int32_t* tris, int T, 
 int mer_project_jvp(const float* tangent_world, int V, const mer_camera* cams, int n, const mer_vertex* vpix,
                     float* tangent_vpix, void* stream);
 
+/* Area-weighted vertex normals, for optimisation loops that shade with normals recomputed from the
+ * current positions (normal supervision, Supp. B): acc [V,3] = sum over the triangles at each vertex of
+ * (p1 - p0) x (p2 - p0), normals [V,3] = acc / max(|acc|, 1e-20).  verts [V,3], tris [T,3] (ids in
+ * [0, V), else MER_ERANGE in status_ws), device FP32; acc is caller-owned scratch kept for the backward. */
+int mer_vertex_normals(const float* verts, int V, const int32_t* tris, int64_t T, float* acc, float* normals,
+                       void* status_ws, void* stream);
+/* Backward of mer_vertex_normals: grad_verts [V,3] += dL/d(verts) given dL/d(normals) in grad_normals
+ * [V,3], which is overwritten (it receives dL/d(acc)).  acc as left by the forward. */
+int mer_vertex_normals_backward(const float* verts, int V, const int32_t* tris, int64_t T, const float* acc,
+                                float* grad_normals, float* grad_verts, void* status_ws, void* stream);
+
 /* ---- Laplacian preconditioning of vertex updates (Nicolet et al. 2021, used by the paper for every mesh
  * optimisation: Sec. 5, Supp. B, lambda = 16) ----
  * Positions x [V,3] are reparameterised as u = M x, M = I + lambda L, with L the combinatorial Laplacian of

@@ -66,6 +66,8 @@ _SIGS = {
     "mer_forward_grad": ([_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P, ctypes.POINTER(MerShading), _I, _P, _P,
                           _P], _I),
     "mer_project_jvp": ([_P, _I, _P, _I, _P, _P, _P], _I),
+    "mer_vertex_normals": ([_P, _I, _P, ctypes.c_int64, _P, _P, _P, _P], _I),
+    "mer_vertex_normals_backward": ([_P, _I, _P, ctypes.c_int64, _P, _P, _P, _P, _P], _I),
     "mer_laplacian_csr": ([_P, ctypes.c_int64, ctypes.c_int64, _P, _P], _I),
     "mer_precond_apply": ([_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P], _I),
     "mer_precond_solve_workspace_size": ([ctypes.c_int64], _Z),
@@ -241,6 +243,17 @@ def mer_project_jvp(tangent_world, cams, vpix, out):
     n, V = vpix.shape[0], vpix.shape[1]
     _check(lib().mer_project_jvp(_ptr(tangent_world), V, _ptr(cams), n, _ptr(vpix), _ptr(out), _stream()),
            "mer_project_jvp")
+
+
+def mer_vertex_normals(verts, tris, acc, normals, status_ws=None):
+    _check(lib().mer_vertex_normals(_ptr(verts), verts.shape[0], _ptr(tris), tris.shape[0], _ptr(acc), _ptr(normals),
+                                    _ptr(status_ws), _stream()), "mer_vertex_normals")
+
+
+def mer_vertex_normals_backward(verts, tris, acc, grad_normals, grad_verts, status_ws=None):
+    _check(lib().mer_vertex_normals_backward(_ptr(verts), verts.shape[0], _ptr(tris), tris.shape[0], _ptr(acc),
+                                             _ptr(grad_normals), _ptr(grad_verts), _ptr(status_ws), _stream()),
+           "mer_vertex_normals_backward")
 
 
 def mer_laplacian_csr(tris: np.ndarray, V: int) -> tuple[np.ndarray, np.ndarray]:

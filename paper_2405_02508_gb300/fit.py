@@ -11,6 +11,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
+from . import binding as B
 from .batch import BatchRenderer
 
 
@@ -34,6 +35,27 @@ class BatchRender(torch.autograd.Function):
         return gv.clone(), ga, None
 
 
+class VertexNormals(torch.autograd.Function):
+    """Area-weighted, normalised vertex normals on the device (mer_vertex_normals and its backward)."""
+
+    @staticmethod
+    def forward(ctx, verts, tris32):
+        verts = verts.contiguous()
+        acc = torch.empty_like(verts)
+        nrm = torch.empty_like(verts)
+        B.mer_vertex_normals(verts, tris32, acc, nrm)
+        ctx.save_for_backward(verts, tris32, acc)
+        return nrm
+
+    @staticmethod
+    def backward(ctx, grad_n):
+        verts, tris32, acc = ctx.saved_tensors
+        g = grad_n.contiguous().clone()
+        gv = torch.zeros_like(verts)
+        B.mer_vertex_normals_backward(verts, tris32, acc, g, gv)
+        return gv, None
+
+
 def vertex_normals(verts: torch.Tensor, tris: torch.Tensor) -> torch.Tensor:
     """Area-weighted, normalised vertex normals (differentiable, PyTorch)."""
     a, b, c = verts[tris[:, 0]], verts[tris[:, 1]], verts[tris[:, 2]]
@@ -54,12 +76,17 @@ class UnevenFit:
         off = np.cumsum([0] + [len(it.verts) for it in items])
         self.vert_off = off
         self.tris_global = torch.from_numpy(np.concatenate([it.tris + off[k] for k, it in enumerate(items)])).long().cuda()
+        self.tris32 = self.tris_global.int().contiguous()
         self.v_true = torch.from_numpy(np.concatenate([it.verts for it in items])).cuda()
         rng = np.random.default_rng(seed)
         self.v_init = self.v_true + torch.from_numpy(rng.normal(0.0, sigma, self.v_true.shape).astype(np.float32)).cuda()
         with torch.no_grad():
-            self.br.prepare(self.v_true, vertex_normals(self.v_true, self.tris_global))
+            self.br.prepare(self.v_true, self.normals(self.v_true))
             self.target = self.br.image.clone()
+
+    def normals(self, x: torch.Tensor) -> torch.Tensor:
+        """Vertex normals of all meshes at positions x (device kernels, differentiable)."""
+        return VertexNormals.apply(x, self.tris32)
 
     @property
     def pixels(self) -> int:
@@ -68,13 +95,13 @@ class UnevenFit:
     @torch.no_grad()
     def loss(self, x: torch.Tensor) -> float:
         """The mask + normal L2 loss at positions x."""
-        self.br.forward(x.contiguous(), vertex_normals(x, self.tris_global).contiguous())
+        self.br.forward(x.contiguous(), self.normals(x).contiguous())
         return float(((self.br.image - self.target) ** 2).sum())
 
     def loss_grad(self, x: torch.Tensor) -> torch.Tensor:
         """dL/dx of the mask + normal L2 loss at positions x (renderer + PyTorch normals)."""
         verts = x.detach().requires_grad_(True)
-        img = BatchRender.apply(verts, vertex_normals(verts, self.tris_global), self.br)
+        img = BatchRender.apply(verts, self.normals(verts), self.br)
         loss = ((img - self.target) ** 2).sum()
         loss.backward()
         return verts.grad
@@ -85,7 +112,7 @@ class UnevenFit:
         opt = torch.optim.Adam([verts], lr=lr)
         for _ in range(steps):
             opt.zero_grad(set_to_none=True)
-            img = BatchRender.apply(verts, vertex_normals(verts, self.tris_global), self.br)
+            img = BatchRender.apply(verts, self.normals(verts), self.br)
             loss = ((img - self.target) ** 2).sum()
             loss.backward()
             opt.step()
