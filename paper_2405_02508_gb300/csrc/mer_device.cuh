@@ -479,6 +479,19 @@ __device__ __forceinline__ int find_item(const mer_item* __restrict__ items, int
     return lo;
 }
 
+// find_item for one element per thread of a 1-D block: one search for the block's first element g0, then
+// each thread steps forward over the (few) item boundaries inside the block.  All threads of the block
+// must call it (it holds a barrier), also those whose element is past the end.
+__device__ __forceinline__ int block_find_item(const mer_item* __restrict__ items, int n, long long g0, long long g,
+                                               int f) {
+    __shared__ int s_k;
+    if (threadIdx.x == 0) s_k = find_item(items, n, g0, f);
+    __syncthreads();
+    int k = s_k;
+    while (k + 1 < n && item_key(items[k + 1], f) <= g) ++k;
+    return k;
+}
+
 __device__ __forceinline__ void set_status(void* ws, int bit) {
     if (ws) atomicOr(&reinterpret_cast<WsHeader*>(ws)->status, bit);
 }

@@ -58,8 +58,9 @@ __global__ void k_project_batch(const float* __restrict__ verts, const mer_camer
                                 const mer_item* __restrict__ items, int n_items, long long vrecs,
                                 mer_vertex* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = block_find_item(items, n_items, (long long)blockIdx.x * blockDim.x, i, kFieldVrec);
     if (i >= vrecs) return;
-    const mer_item m = items[find_item(items, n_items, i, kFieldVrec)];
+    const mer_item m = items[k];
     project_one(verts + 3 * (size_t)(m.vert + (i - m.vrec)), cams[m.cam], out + i);
 }
 
@@ -92,8 +93,9 @@ __global__ void k_project_backward_batch(const mer_camera* __restrict__ cams, co
                                          int n_items, long long vrecs, const mer_vertex* __restrict__ vpix,
                                          const double* __restrict__ grad_vpix, float* __restrict__ grad_verts) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = block_find_item(items, n_items, (long long)blockIdx.x * blockDim.x, i, kFieldVrec);
     if (i >= vrecs) return;
-    const mer_item m = items[find_item(items, n_items, i, kFieldVrec)];
+    const mer_item m = items[k];
     float w[3];
     if (!world_grad(vpix[i], cams[m.cam], grad_vpix + 3 * i, w)) return;
     float* o = grad_verts + 3 * (size_t)(m.vert + (i - m.vrec));

@@ -425,8 +425,8 @@ __device__ __forceinline__ RItem batch_item(const mer_item& m, int tile, const m
 __global__ void k_setup_count_batch(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris, BatchGeom b,
                                     TriRaster* __restrict__ recs, int* __restrict__ counts, void* ws) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = block_find_item(b.items, b.n_items, (long long)blockIdx.x * blockDim.x, i, kFieldTrec);
     if (i >= b.trecs) return;
-    const int k = find_item(b.items, b.n_items, i, kFieldTrec);
     const mer_item m = b.items[k];
     setup_count_one(batch_item(m, b.tile, vpix, tris, recs), (int)(i - m.trec), b.tile, counts, ws);
 }
@@ -436,8 +436,8 @@ __global__ void k_bin_fill_batch(const mer_vertex* __restrict__ vpix, const int*
                                  const int* __restrict__ counts, int* __restrict__ cursor, int* __restrict__ list,
                                  long long capacity) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = block_find_item(b.items, b.n_items, (long long)blockIdx.x * blockDim.x, i, kFieldTrec);
     if (i >= b.trecs) return;
-    const int k = find_item(b.items, b.n_items, i, kFieldTrec);
     const mer_item m = b.items[k];
     fill_one(batch_item(m, b.tile, vpix, tris, recs), (int)(i - m.trec), b.tile, offs, counts, cursor,
              cursor + b.tiles, list, capacity);

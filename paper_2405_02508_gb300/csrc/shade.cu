@@ -36,8 +36,9 @@ __global__ void k_shade_batch(const mer_vertex* __restrict__ vpix, const int* __
                               const int* __restrict__ index, const float* __restrict__ attr,
                               const float* __restrict__ tex, ShadeArgs a, float* __restrict__ image, void* ws) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = block_find_item(items, n_items, (long long)blockIdx.x * blockDim.x, p, kFieldPix);
     if (p >= pixels) return;
-    const mer_item m = items[find_item(items, n_items, p, kFieldPix)];
+    const mer_item m = items[k];
     const int rem = (int)(p - m.pix);
     shade_pixel(vpix + m.vrec, m.V, tris + 3 * m.tri, m.T, rem % m.W, rem / m.W, (size_t)p, index,
                 attr ? attr + (size_t)m.vert * a.sh.C_attr : nullptr, tex, a, image, ws);

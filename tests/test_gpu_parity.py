@@ -324,6 +324,37 @@ def test_recompute_bary_bitwise_identical():
     np.testing.assert_allclose(a.grad_verts, b.grad_verts, rtol=1e-5, atol=1e-6 * np.abs(a.grad_verts).max())
 
 
+def test_recompute_option_peak_memory():
+    """Head-scale single view (1024^2, 131k triangles) through the autograd function: storing the barycentric
+    image costs its 8 B per pixel of peak device memory, recomputing it in the backward does not, and the
+    gradients agree."""
+    import torch
+
+    from paper_2405_02508_gb300 import binding as B
+    from paper_2405_02508_gb300.render import MerRender, Renderer
+
+    sc = scenes.head_single_view()
+    tex = torch.from_numpy(sc.tex).cuda()
+    cams = B.cameras_tensor(sc.cams)
+    g = torch.from_numpy(sc.upstream()).cuda()
+    r = Renderer(torch.from_numpy(sc.tris), len(sc.verts), 1, sc.H, sc.W, sc.shading, 2, tex.shape)
+    peak, grads = {}, {}
+    for recompute in (True, False, True):
+        verts = torch.from_numpy(sc.verts).cuda().requires_grad_(True)
+        attr = torch.from_numpy(sc.attr).cuda().requires_grad_(True)
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        img = MerRender.apply(verts, attr, tex, cams, r, recompute)
+        (img * g).sum().backward()
+        torch.cuda.synchronize()
+        peak[recompute] = torch.cuda.max_memory_allocated() - base
+        grads[recompute] = verts.grad.cpu().numpy()
+    print(f"peak extra memory: recompute {peak[True] / 2**20:.1f} MiB, stored bary {peak[False] / 2**20:.1f} MiB")
+    assert peak[False] - peak[True] >= 8 * sc.H * sc.W
+    np.testing.assert_allclose(grads[True], grads[False], rtol=1e-5, atol=1e-6 * np.abs(grads[False]).max())
+
+
 def test_modular_entry_points_sum_to_fused(orc):
     """mer_edge_grad_backward + mer_interpolate_backward reproduce the fused backward (plain interpolation)."""
     import torch
