@@ -307,6 +307,10 @@ int mer_vertex_normals(const float* verts, int V, const int32_t* tris, int64_t T
 int mer_vertex_normals_backward(const float* verts, int V, const int32_t* tris, int64_t T, const float* acc,
                                 float* grad_normals, float* grad_verts, void* status_ws, void* stream);
 
+/* L2 image loss of an inverse-rendering loop and its gradient in one pass over n floats (device):
+ * grad = 2 (image - target) and *loss += sum (image - target)^2 (FP64, device scalar the caller zeroes). */
+int mer_l2_loss_grad(const float* image, const float* target, int64_t n, float* grad, double* loss, void* stream);
+
 /* ---- Laplacian preconditioning of vertex updates (Nicolet et al. 2021, used by the paper for every mesh
  * optimisation: Sec. 5, Supp. B, lambda = 16) ----
  * Positions x [V,3] are reparameterised as u = M x, M = I + lambda L, with L the combinatorial Laplacian of

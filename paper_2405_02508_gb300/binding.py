@@ -68,6 +68,7 @@ _SIGS = {
     "mer_project_jvp": ([_P, _I, _P, _I, _P, _P, _P], _I),
     "mer_vertex_normals": ([_P, _I, _P, ctypes.c_int64, _P, _P, _P, _P], _I),
     "mer_vertex_normals_backward": ([_P, _I, _P, ctypes.c_int64, _P, _P, _P, _P, _P], _I),
+    "mer_l2_loss_grad": ([_P, _P, ctypes.c_int64, _P, _P, _P], _I),
     "mer_laplacian_csr": ([_P, ctypes.c_int64, ctypes.c_int64, _P, _P], _I),
     "mer_precond_apply": ([_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P], _I),
     "mer_precond_solve_workspace_size": ([ctypes.c_int64], _Z),
@@ -254,6 +255,11 @@ def mer_vertex_normals_backward(verts, tris, acc, grad_normals, grad_verts, stat
     _check(lib().mer_vertex_normals_backward(_ptr(verts), verts.shape[0], _ptr(tris), tris.shape[0], _ptr(acc),
                                              _ptr(grad_normals), _ptr(grad_verts), _ptr(status_ws), _stream()),
            "mer_vertex_normals_backward")
+
+
+def mer_l2_loss_grad(image, target, grad, loss):
+    _check(lib().mer_l2_loss_grad(_ptr(image), _ptr(target), image.numel(), _ptr(grad), _ptr(loss), _stream()),
+           "mer_l2_loss_grad")
 
 
 def mer_laplacian_csr(tris: np.ndarray, V: int) -> tuple[np.ndarray, np.ndarray]:

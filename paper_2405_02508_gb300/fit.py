@@ -95,26 +95,44 @@ class UnevenFit:
     @torch.no_grad()
     def loss(self, x: torch.Tensor) -> float:
         """The mask + normal L2 loss at positions x."""
-        self.br.forward(x.contiguous(), self.normals(x).contiguous())
-        return float(((self.br.image - self.target) ** 2).sum())
+        self._render(x.contiguous())
+        self._l2()
+        return float(self._loss.item())
 
+    def _render(self, x: torch.Tensor) -> torch.Tensor:
+        """Normals (kept for the backward) and the batched render at positions x; returns the normals."""
+        if getattr(self, "_nacc", None) is None or self._nacc.shape != x.shape:
+            self._nacc = torch.empty_like(x)
+            self._nrm = torch.empty_like(x)
+            self._gimg = torch.empty_like(self.target)
+            self._loss = torch.zeros(1, dtype=torch.float64, device=x.device)
+        B.mer_vertex_normals(x, self.tris32, self._nacc, self._nrm)
+        self.br.forward(x, self._nrm)
+        return self._nrm
+
+    def _l2(self):
+        self._loss.zero_()
+        B.mer_l2_loss_grad(self.br.image, self.target, self._gimg, self._loss)
+
+    @torch.no_grad()
     def loss_grad(self, x: torch.Tensor) -> torch.Tensor:
-        """dL/dx of the mask + normal L2 loss at positions x (renderer + PyTorch normals)."""
-        verts = x.detach().requires_grad_(True)
-        img = BatchRender.apply(verts, self.normals(verts), self.br)
-        loss = ((img - self.target) ** 2).sum()
-        loss.backward()
-        return verts.grad
+        """dL/dx of the mask + normal L2 loss at positions x, all in device kernels: normals, render, the loss
+        gradient, the micro-edge + interior backward (positions and normals), the normals' backward.  The
+        returned tensor is the renderer's buffer, valid until the next call."""
+        x = x.contiguous()
+        nrm = self._render(x)
+        self._l2()
+        ga = torch.zeros_like(nrm)
+        gv = self.br.backward(self._gimg, nrm, grad_attr=ga)
+        B.mer_vertex_normals_backward(x, self.tris32, self._nacc, ga, gv)
+        return gv
 
     def run(self, steps: int, lr: float = 1e-3):
         """Plain per-vertex Adam on the positions."""
         verts = self.v_init.clone().requires_grad_(True)
         opt = torch.optim.Adam([verts], lr=lr)
         for _ in range(steps):
-            opt.zero_grad(set_to_none=True)
-            img = BatchRender.apply(verts, self.normals(verts), self.br)
-            loss = ((img - self.target) ** 2).sum()
-            loss.backward()
+            verts.grad = self.loss_grad(verts.detach())
             opt.step()
         return verts.detach()
 
