@@ -22,12 +22,21 @@ __global__ void k_l2_loss_grad(const float* __restrict__ image, const float* __r
         const float4* a4 = reinterpret_cast<const float4*>(image);
         const float4* b4 = reinterpret_cast<const float4*>(target);
         float4* g4 = reinterpret_cast<float4*>(grad);
+        // FP32 partial sums of 32 groups go to the FP64 total (the FP64 pipe is narrow on this GPU)
+        float part = 0.f;
+        int k = 0;
         for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
             const float4 a = a4[i], b = b4[i];
             const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
             g4[i] = make_float4(2.f * d0, 2.f * d1, 2.f * d2, 2.f * d3);
-            acc += (double)(d0 * d0) + (double)(d1 * d1) + (double)(d2 * d2) + (double)(d3 * d3);
+            part += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
+            if (++k == 32) {
+                acc += (double)part;
+                part = 0.f;
+                k = 0;
+            }
         }
+        acc += (double)part;
         done = n4 * 4;
     }
     for (long long i = done + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {

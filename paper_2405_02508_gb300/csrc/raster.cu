@@ -103,6 +103,13 @@ __device__ __forceinline__ void setup_count_one(const RItem& it, int t, int tile
     r.bx0 = (short)x0; r.bx1 = (short)x1; r.by0 = (short)y0; r.by1 = (short)y1;
     it.recs[t] = r;
     int* cnt = counts + it.tile0;
+    if (y0 / tile == y1 / tile && x0 / tile == x1 / tile) {
+        // one bin tile (the common case): lanes of the warp counting into the same tile add once together
+        int* c = cnt + (y0 / tile) * it.ntx + x0 / tile;
+        const unsigned peers = __match_any_sync(__activemask(), (unsigned long long)c);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(c, __popc(peers));
+        return;
+    }
     for (int ty = y0 / tile; ty <= y1 / tile; ++ty)
         for (int tx = x0 / tile; tx <= x1 / tile; ++tx) atomicAdd(cnt + ty * it.ntx + tx, 1);
 }
@@ -116,6 +123,19 @@ __device__ __forceinline__ void fill_one(const RItem& it, int t, int tile, const
     const TriRaster& r = it.recs[t];
     if (r.flags < 0) return;
     const bool front = (r.flags & 8) != 0;
+    if (r.by0 / tile == r.by1 / tile && r.bx0 / tile == r.bx1 / tile) {
+        // one bin tile: lanes filling the same (tile, part) take consecutive positions with one atomic
+        const size_t g = it.tile0 + (size_t)(r.by0 / tile) * it.ntx + r.bx0 / tile;
+        int* cur = front ? cursor + g : cursor_back + g;
+        const unsigned peers = __match_any_sync(__activemask(), (unsigned long long)cur);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(cur, __popc(peers));
+        base = __shfl_sync(peers, base, leader) + __popc(peers & ((1u << lane) - 1u));
+        const long long pos = front ? (long long)offs[g] + base : (long long)offs[g] + counts[g] - 1 - base;
+        if (pos < capacity) list[pos] = t;
+        return;
+    }
     for (int ty = r.by0 / tile; ty <= r.by1 / tile; ++ty)
         for (int tx = r.bx0 / tile; tx <= r.bx1 / tile; ++tx) {
             const size_t g = it.tile0 + (size_t)ty * it.ntx + tx;
