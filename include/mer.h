@@ -137,6 +137,12 @@ int mer_project_screen(const double* scr, int V, int n, mer_vertex* vpix, void* 
 int mer_rasterize(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
                   int tile, void* workspace, size_t workspace_bytes,
                   int32_t* index, float* depth, float* bary, void* stream);
+/* mer_project followed by mer_rasterize: world-space vertices [V,3] and n cameras in, index / depth /
+ * bary out, the projected records written to vpix [n,V] (the other calls take them).  Arguments, errors and
+ * workspace as the two calls. */
+int mer_rasterize_world(const float* verts, int V, const int32_t* tris, int T, const mer_camera* cams, int n,
+                        int H, int W, int tile, void* workspace, size_t workspace_bytes, int32_t* index,
+                        float* depth, float* bary, mer_vertex* vpix, void* stream);
 
 /* mer_rasterize without a workspace argument, for callers that cannot allocate device memory at the
  * time they call -- code running while a stream is being captured into a CUDA graph (cudaMalloc is not

@@ -69,6 +69,7 @@ _SIGS = {
     "mer_vertex_normals": ([_P, _I, _P, ctypes.c_int64, _P, _P, _P, _P], _I),
     "mer_vertex_normals_backward": ([_P, _I, _P, ctypes.c_int64, _P, _P, _P, _P, _P], _I),
     "mer_l2_loss_grad": ([_P, _P, ctypes.c_int64, _P, _P, _P], _I),
+    "mer_rasterize_world": ([_P, _I, _P, _I, _P, _I, _I, _I, _I, _P, _Z, _P, _P, _P, _P, _P], _I),
     "mer_laplacian_csr": ([_P, ctypes.c_int64, ctypes.c_int64, _P, _P], _I),
     "mer_precond_apply": ([_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P], _I),
     "mer_precond_solve_workspace_size": ([ctypes.c_int64], _Z),
@@ -260,6 +261,13 @@ def mer_vertex_normals_backward(verts, tris, acc, grad_normals, grad_verts, stat
 def mer_l2_loss_grad(image, target, grad, loss):
     _check(lib().mer_l2_loss_grad(_ptr(image), _ptr(target), image.numel(), _ptr(grad), _ptr(loss), _stream()),
            "mer_l2_loss_grad")
+
+
+def mer_rasterize_world(verts, tris, cams, H, W, tile, workspace, index, vpix, depth=None, bary=None):
+    n, V = vpix.shape[0], vpix.shape[1]
+    _check(lib().mer_rasterize_world(_ptr(verts), V, _ptr(tris), tris.shape[0], _ptr(cams), n, H, W, tile,
+                                     _ptr(workspace), workspace.numel() * workspace.element_size(), _ptr(index),
+                                     _ptr(depth), _ptr(bary), _ptr(vpix), _stream()), "mer_rasterize_world")
 
 
 def mer_laplacian_csr(tris: np.ndarray, V: int) -> tuple[np.ndarray, np.ndarray]:

@@ -100,6 +100,17 @@ int mer_project(const float* verts, int V, const mer_camera* cams, int n, mer_ve
     return mer_launch_project(verts, V, cams, n, vpix, S(stream));
 }
 
+int mer_rasterize_world(const float* verts, int V, const int32_t* tris, int T, const mer_camera* cams, int n, int H,
+                        int W, int tile, void* workspace, size_t workspace_bytes, int32_t* index, float* depth,
+                        float* bary, mer_vertex* vpix, void* stream) {
+    if (V < 0 || T < 0 || !dims_ok(n, H, W)) return MER_EINVAL;
+    if ((long long)n * H * W == 0) return MER_OK;
+    if (V > 0 && (!verts || !cams || !vpix)) return MER_EINVAL;
+    const int rc = mer_project(verts, V, cams, n, vpix, stream);
+    if (rc != MER_OK) return rc;
+    return mer_rasterize(vpix, V, tris, T, n, H, W, tile, workspace, workspace_bytes, index, depth, bary, stream);
+}
+
 int mer_project_screen(const double* scr, int V, int n, mer_vertex* vpix, void* stream) {
     if (V < 0 || n < 0) return MER_EINVAL;
     if ((long long)V * n == 0) return MER_OK;

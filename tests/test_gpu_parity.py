@@ -324,6 +324,29 @@ def test_recompute_bary_bitwise_identical():
     np.testing.assert_allclose(a.grad_verts, b.grad_verts, rtol=1e-5, atol=1e-6 * np.abs(a.grad_verts).max())
 
 
+def test_rasterize_world_equals_project_then_rasterize():
+    """The one-call entry point (world vertices + cameras) gives the same index, depth and records."""
+    import torch
+
+    from paper_2405_02508_gb300 import binding as B
+    from paper_2405_02508_gb300.render import Renderer
+
+    sc = scenes.head_multiview(n_views=3, H=200, W=160, n=24, tex_size=32)
+    verts = torch.from_numpy(sc.verts).cuda()
+    cams = B.cameras_tensor(sc.cams)
+    r = Renderer(torch.from_numpy(sc.tris), len(sc.verts), 3, 200, 160, sc.shading, 2, sc.tex.shape)
+    depth = torch.empty((3, 200, 160), device="cuda")
+    r.project(verts, cams)
+    r.rasterize(depth)
+    idx0, d0, v0 = r.index.clone(), depth.clone(), r.vpix.clone()
+    r.index.fill_(-7)
+    r.vpix.zero_()
+    B.mer_rasterize_world(verts, r.tris, cams, 200, 160, r.tile, r.workspace, r.index, r.vpix, depth)
+    r.check_status()
+    assert torch.equal(r.index, idx0) and torch.equal(depth, d0)
+    assert torch.equal(r.vpix.view(torch.int32), v0.view(torch.int32))  # records hold integer fields
+
+
 def test_recompute_option_peak_memory():
     """Head-scale single view (1024^2, 131k triangles) through the autograd function: storing the barycentric
     image costs its 8 B per pixel of peak device memory, recomputing it in the backward does not, and the
