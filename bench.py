@@ -38,8 +38,10 @@ def parse():
     ap.add_argument("--views", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the per-view launch path")
-    ap.add_argument("--workload", default="multiview", choices=["multiview", "uneven"],
-                    help="multiview: 32 views of the head mesh (default); uneven: 256-mesh Adam fitting loop")
+    ap.add_argument("--workload", default="multiview", choices=["multiview", "uneven", "configs"],
+                    help="multiview: 32 views of the head mesh (default); uneven: 256-mesh Adam fitting loop; "
+                         "configs: one line per single-view config (tiny, intersection, head-scale) with the "
+                         "batched and per-view paths and the oracle on 1 and all host threads")
     ap.add_argument("--items", type=int, default=256)
     return ap.parse_args()
 
@@ -242,6 +244,91 @@ def run_uneven(args):
         dist.destroy_process_group()
 
 
+def run_configs(args):
+    """Side table (not the headline): the single-view configurations through the batched graph path and the
+    per-view launch path, with the FP64 oracle on one host thread and on all of them."""
+    import torch
+
+    from paper_2405_02508_gb300 import binding as B
+    from paper_2405_02508_gb300 import scenes
+    from paper_2405_02508_gb300.batch import BatchRenderer, PlainRenderer
+
+    torch.cuda.set_device(0)
+    B.lib()
+    cases = [("tiny icosphere 128x128, 1280 tris, RGB", scenes.tiny_icosphere()),
+             ("two interpenetrating icospheres 512x512, 40960 tris, normals+mask+depth", scenes.two_spheres()),
+             ("head-scale single view 1024x1024, 131072 tris, textured RGB+mask", scenes.head_single_view())]
+    threads = min(os.cpu_count() or 1, 8)
+    for name, sc in cases:
+        H, W, C = sc.H, sc.W, sc.shading.C
+        verts = torch.from_numpy(sc.verts).cuda()
+        attr = torch.from_numpy(sc.attr).cuda()
+        tex = torch.from_numpy(sc.tex).cuda() if sc.tex is not None else None
+        g = torch.from_numpy(sc.upstream()).cuda().reshape(-1, C)
+        br = BatchRenderer([(sc.verts, sc.tris)], [(0, 0, H, W)], sc.cams, sc.shading, sc.attr.shape[1], tex, tile=32)
+        br.prepare(verts, attr, tex)
+        br.capture(verts, attr, g, tex)
+        pr = PlainRenderer([(sc.verts, sc.tris)], [(0, 0, H, W)], sc.cams, sc.shading, sc.attr.shape[1],
+                           None if tex is None else tex.shape, tile=16)
+        gv = [g.view(1, H, W, C)]
+        pr.step([verts], [attr], gv, tex, checked=True)
+
+        def timed(fn, reps):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        reps = max(args.steps, 20)
+        ms_b = timed(br.replay, reps)
+        ms_p = timed(lambda: pr.step([verts], [attr], gv, tex), reps)
+        px = H * W
+        fwd = px * (4 + 4 + 4 * C) + len(sc.tris) * 12 + len(sc.verts) * 32
+        bwd = px * (4 + 8 * C) + len(sc.verts) * 44
+        peak, kind = peaks()
+        cpu1, dt1 = oracle_sample(sc, 1, 1)
+        line = {"workload": name, "metric": METRIC, "unit": "Mpix/s", "batched": px / (ms_b * 1e-3) / 1e6,
+                "batched_ms": ms_b, "plain": px / (ms_p * 1e-3) / 1e6, "plain_ms": ms_p,
+                "algorithmic_gbs": (fwd + bwd) / (ms_b * 1e-3) / 1e9,
+                "roofline_frac": (fwd + bwd) / (ms_b * 1e-3) / 1e9 / peak, "peak_gbs": peak, "peak_kind": kind,
+                "cpu_oracle_1thread": {"value": cpu1, "unit": "Mpix/s", "seconds": dt1},
+                "cpu_oracle_note": f"one view: {threads} threads cannot split it (views are the unit of the pool)"}
+        print(json.dumps(line), flush=True)
+        del br, pr
+        torch.cuda.empty_cache()
+    # the oracle on the two batched workloads: one view of the multi-view scene on one thread, and one full
+    # step over all 256 meshes of the uneven batch on all threads
+    mv = scenes.head_multiview(n_views=1)
+    v1, d1 = oracle_sample(mv, 1, 1)
+    print(json.dumps({"workload": "head multi-view, 1 of 32 views 1334x2048", "cpu_oracle_1thread":
+                      {"value": v1, "unit": "Mpix/s", "seconds": d1}}), flush=True)
+    import oracle
+
+    items = scenes.uneven_batch(n_items=args.items)
+    t0 = time.perf_counter()
+
+    def one(it):
+        r = oracle.render(it)[0]
+        g = it.upstream()[0]
+        oracle.backward(r.scr, r.snap, r.flags, it.tris, r.index, r.image, g, it.attr, it.shading, want_attr=True)
+
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, items))
+    dt = time.perf_counter() - t0
+    px = sum(it.H * it.W for it in items)
+    print(json.dumps({"workload": f"uneven batch, one full step over {len(items)} meshes",
+                      "cpu_oracle_all_threads": {"value": px / dt / 1e6, "unit": "Mpix/s", "seconds": dt,
+                                                 "cores": threads}}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -249,6 +336,9 @@ def main():
         return
     if args.workload == "uneven":
         run_uneven(args)
+        return
+    if args.workload == "configs":
+        run_configs(args)
         return
     import torch
     import torch.distributed as dist
