@@ -352,7 +352,7 @@ def main():
 
     from paper_2405_02508_gb300 import binding as B
     from paper_2405_02508_gb300 import scenes
-    from paper_2405_02508_gb300.batch import BatchRenderer, PlainRenderer, autotune_tile, workload_key
+    from paper_2405_02508_gb300.batch import BatchRenderer, PlainRenderer, autotune, workload_key
 
     B.lib()
     dev = "cuda"
@@ -370,16 +370,17 @@ def main():
     items = [(0, v, H, W) for v in range(n)]
     stream = torch.cuda.current_stream()
 
-    def make(tile):
-        br = BatchRenderer(meshes, items, scene.cams, scene.shading, attr.shape[1], tex, tile=tile)
+    def make(tile, ctas=0):
+        br = BatchRenderer(meshes, items, scene.cams, scene.shading, attr.shape[1], tex, tile=tile,
+                           persistent_ctas=ctas)
         br.prepare(verts, attr, tex)
         return br
 
     if args.tile > 0:
-        tile, tune = args.tile, {}
-    else:  # autotuned bin tile, cached per workload signature
-        tile, tune = autotune_tile(make, lambda r: r.step(verts, attr, g, tex), key=workload_key(items, meshes))
-    br = make(tile)
+        tile, ctas, tune = args.tile, 0, {}
+    else:  # autotuned bin tile and persistent grid, cached per workload signature
+        tile, ctas, tune = autotune(make, lambda r: r.step(verts, attr, g, tex), key=workload_key(items, meshes))
+    br = make(tile, ctas)
     br.capture(verts, attr, g, tex)  # one CUDA graph: the whole forward + backward step
 
     for _ in range(args.warmup):
@@ -468,7 +469,7 @@ def main():
         "config": {"workload": f"head multi-view: {n} views x {W}x{H}, {V} verts / {T} tris, 1024^2 texture, "
                                f"RGB+mask+depth (C={C}), upstream N(0,1)", "views_per_gpu": n, "H": H, "W": W,
                    "triangles": T, "path": "batched: persistent raster/backward over a device tile queue, "
-                   "one CUDA graph per step", "tile": tile, "tile_autotune_ms": tune,
+                   "one CUDA graph per step", "tile": tile, "persistent_ctas": br.persistent_ctas, "autotune_ms (tile/ctas)": tune,
                    "l2": "inputs larger than L2 (images 1.7 GB per step)", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": "k_backward_batch (fused edge + interior)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": backward_traffic(n * H * W),

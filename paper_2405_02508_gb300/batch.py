@@ -220,6 +220,49 @@ def autotune_tile(make_renderer, run_step, candidates=(16, 32, 64), reps: int = 
     return best, times
 
 
+def autotune(make_renderer, run_step, tiles=(16, 32, 64), ctas_per_sm=(2, 4), reps: int = 3, key: str | None = None,
+             cache_file: str | None = _CACHE_FILE) -> tuple[int, int, dict]:
+    """Bin tile size and work split (persistent CTAs of the raster and backward grids) by timing one step per
+    candidate pair -> (tile, persistent CTAs, {"tile/ctas": ms}).  make_renderer(tile, ctas) builds a
+    renderer; the result is cached under ``key`` like autotune_tile's."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    cache = {}
+    if key and cache_file and os.path.exists(cache_file):
+        try:
+            with open(cache_file) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    ckey = None if key is None else key + "_split"
+    if ckey and ckey in cache:
+        return int(cache[ckey]["tile"]), int(cache[ckey]["ctas"]), cache[ckey]["ms"]
+    times = {}
+    for tile in tiles:
+        for c in ctas_per_sm:
+            r = make_renderer(tile, sms * c)
+            run_step(r)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                run_step(r)
+            e1.record()
+            torch.cuda.synchronize()
+            times[f"{tile}/{sms * c}"] = e0.elapsed_time(e1) / reps
+            del r
+    best = min(times, key=times.get)
+    tile, ctas = (int(v) for v in best.split("/"))
+    if ckey and cache_file:
+        cache[ckey] = {"tile": tile, "ctas": ctas, "ms": times}
+        try:
+            os.makedirs(os.path.dirname(cache_file), exist_ok=True)
+            with open(cache_file, "w") as f:
+                json.dump(cache, f)
+        except OSError:
+            pass
+    return tile, ctas, times
+
+
 def workload_key(items, meshes) -> str:
     """Autotune signature: triangle and pixel totals rounded to powers of two."""
     T = sum(len(meshes[m][1]) for (m, _, _, _) in items)

@@ -170,3 +170,13 @@ def test_autotune_picks_a_candidate():
 
     best, times = autotune_tile(make, lambda r: r.step(verts, attr, g, tex), cache_file=None)
     assert best in (16, 32, 64) and set(times) == {16, 32, 64}
+    from paper_2405_02508_gb300.batch import autotune
+
+    def make2(tile, ctas):
+        br = make(tile)
+        br.persistent_ctas = ctas
+        return br
+
+    tile, ctas, t2 = autotune(make2, lambda r: r.step(verts, attr, g, tex), tiles=(16, 32), cache_file=None)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert tile in (16, 32) and ctas in (2 * sms, 4 * sms) and len(t2) == 4
