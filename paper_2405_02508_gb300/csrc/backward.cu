@@ -153,7 +153,6 @@ __device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, Bwd
         const int r = i - (d == 0 ? 0 : (d == 1 ? n0 : (d == 2 ? n1 : n2)));
         const unsigned md = d == 0 ? m[0] : (d == 1 ? m[1] : (d == 2 ? m[2] : m[3]));
         const int src = i < n ? (int)__fns(md, 0, r + 1) : lane;
-        const int ts = __shfl_sync(full, t, src);
         int vs[3], Xs[3], Ys[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -253,7 +252,6 @@ __device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, Bwd
             if (axis == 0) ex = kk * nv0; else ey = kk * nv0;
             ez = kk * nv1;
         }
-        (void)ts;
         atomicAdd(acc + 3 * src, ex);
         atomicAdd(acc + 3 * src + 1, ey);
         atomicAdd(acc + 3 * src + 2, ez);

@@ -46,9 +46,9 @@ MUTATIONS = {
 def test_pins_catch_planted_mistake(name, tmp_path):
     old, new = MUTATIONS[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, name
+    assert src.count(old) >= 1, name  # the first occurrence: the backward (a copy may sit in the forward gradients)
     mutated = tmp_path / "oracle_mut.c"
-    mutated.write_text(src.replace(old, new))
+    mutated.write_text(src.replace(old, new, 1))
     lib = tmp_path / "liboracle_mut.so"
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(lib),
                     str(mutated), "-lm"], check=True)

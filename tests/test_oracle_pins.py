@@ -679,7 +679,7 @@ def test_backface_loss_ramp_identity(orc, winding):
 
 
 # ---------------------------------------------------------------------------
-# Exact-crossing gather weights (the survey's f4 option): same identities, faster convergence
+# Exact-crossing gather weights (an option): same identities, faster convergence
 # ---------------------------------------------------------------------------
 
 EXACT_CROSSING = 8
