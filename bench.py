@@ -112,8 +112,8 @@ class ClockSampler:
 # of the same workload at 4 views (inputs already larger than L2), per pixel of the launch, with the sha256 of
 # the kernel's sources it was taken on: a launch of n views moves n*H*W times this.  It is reported only while
 # the sources are unchanged.
-BACKWARD_TRAFFIC = {"bytes_per_pixel": 22.8828,
-                    "sources_sha256": "101d079c102859967ae6982b1fdb2e58ae476a2f5f035c7f7c78492231330af1",
+BACKWARD_TRAFFIC = {"bytes_per_pixel": 22.9189,
+                    "sources_sha256": "d0e4bb5679b1e4a65be8b67edbae6502ea7fe6f33fe64f65871dac21f04f55bc",
                     "profile": "profiles/ncu_k_backward_batch_head_4x1334x2048.md"}
 
 
