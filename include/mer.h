@@ -14,7 +14,9 @@
  * Conventions shared by every call
  * --------------------------------
  * - Every pointer argument except where stated is a DEVICE pointer.  The caller
- *   owns all memory, including the workspace; the library allocates nothing.
+ *   owns all memory, including the workspace; the library allocates no device
+ *   memory at call time (mer_rasterize_noalloc uses a static device array that
+ *   exists from load time; the host call mer_laplacian_csr uses host scratch).
  * - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
  *   NULL = the legacy default stream).  A call returns MER_OK after queueing its
  *   kernels; argument errors found on the host return at once, without launching.
@@ -176,7 +178,7 @@ int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, 
 
 /* Backward pass.  image / grad_image [n,H,W,C] are the shaded image passed
  * through the edge-gradient step and dL/d(image).  terms = MER_EDGE |
- * MER_INTERIOR | MER_INTERSECT (any subset).
+ * MER_INTERIOR | MER_INTERSECT (any subset), optionally | MER_EXACT_CROSSING.
  *   MER_EDGE: every pair (x,y)-(x+1,y), (x,y)-(x,y+1) with differing ids:
  *     Eq. 11 summed over channels; classification by the exact coverage test of
  *     each pixel centre against the other pixel's triangle (Sec. 4.3): none ->

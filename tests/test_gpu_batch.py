@@ -128,6 +128,44 @@ def test_batch_uneven_items_against_oracle(orc):
         assert nbad == 0, (k, worst)
 
 
+def test_full_uneven_batch_in_bench_configuration(orc):
+    """The whole 256-mesh uneven batch (500..200k triangles, 128^2..1024^2) in one batched pass with the
+    bench's 32 px tile and default grid; the smallest, the largest and two middle items against the oracle."""
+    import torch
+
+    from paper_2405_02508_gb300.batch import BatchRenderer
+
+    its = scenes.uneven_batch(n_items=256)
+    sh = its[0].shading
+    br = BatchRenderer([(it.verts, it.tris) for it in its], [(k, k, it.H, it.W) for k, it in enumerate(its)],
+                       np.concatenate([it.cams for it in its]), sh, 3, None, tile=32)
+    verts = torch.from_numpy(np.concatenate([it.verts for it in its])).cuda()
+    attr = torch.from_numpy(np.concatenate([it.attr for it in its])).cuda()
+    grads = {}
+    br.prepare(verts, attr)
+    T = np.array([len(it.tris) for it in its])
+    order = np.argsort(T)
+    picks = [int(order[0]), int(order[85]), int(order[170]), int(order[-1])]
+    g = torch.zeros((int(br.tot.pixels), sh.C), device="cuda")
+    for k in picks:
+        p0, H, W = br.item_pix[k]
+        grads[k] = its[k].upstream()[0]
+        g[p0:p0 + H * W] = torch.from_numpy(grads[k].reshape(-1, sh.C)).cuda()
+    br.backward(g, attr)
+    br.check()
+    for k in picks:
+        it = its[k]
+        ov = orc.render(it)[0]
+        gs, _, cnt, S = orc.backward(ov.scr, ov.snap, ov.flags, it.tris, ov.index, ov.image, grads[k], it.attr, sh,
+                                     want_abs=True)
+        gi = br.item_index(k).cpu().numpy()
+        assert np.all((gi == ov.index) | ov.tie)
+        np.testing.assert_allclose(br.item_image(k).cpu().numpy(), ov.image, rtol=parity.IMG_TOL, atol=parity.IMG_TOL)
+        ex = parity.excluded_vertices(it.tris, gi, ov.index)
+        nbad, worst = parity.grad_violations(br.item_grad_vpix(k).cpu().numpy(), gs, S, ex)
+        assert nbad == 0, (k, worst)
+
+
 def test_batch_graph_replay_matches_eager():
     import torch
 
