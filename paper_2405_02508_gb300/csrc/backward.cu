@@ -91,14 +91,14 @@ struct BItem {
     int V, T, H, W;
 };
 
-constexpr int kMaxA = 4;  // attribute-gradient channels carried through the per-tile aggregation
+constexpr int kMaxA = 4;  // most attribute-gradient channels carried through the per-tile aggregation
 
-template <bool ATTR, bool EXACT>
+template <int NA, bool EXACT>
 struct BwdShared {
     int sidx[kHH][kHW];
     int skey[kSlots];
     float sval[kSlots][3];
-    float sattr[ATTR ? kSlots : 1][kMaxA];
+    float sattr[NA > 0 ? kSlots : 1][NA > 0 ? NA : 1];
     float efrag[kTH][32][3];  // per warp: edge-term fragment gradients returned to the pixel's lane
     float evert[EXACT ? kTH : 1][32][3][2];  // exact-crossing option: per pixel, (x, y) per triangle vertex
 };
@@ -108,8 +108,8 @@ struct BwdShared {
 // compacted into one list per warp and classified 32 at a time, every lane busy, the source pixel's triangle
 // taken from its lane by shuffle; a pair that scatters to the source fragment adds into that pixel's slot of a
 // per-warp shared buffer, which the owning lane finally adds to (fx, fy, fz).
-template <bool ATTR, bool EXACT>
-__device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, BwdShared<ATTR, EXACT>& S, void* ws, int row,
+template <int NA, bool EXACT>
+__device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, BwdShared<NA, EXACT>& S, void* ws, int row,
                                           int lane, int x, int y, int t, const int vid[3], const int X[3],
                                           const int Y[3], float& fx, float& fy, float& fz) {
     const unsigned full = 0xffffffffu;
@@ -267,22 +267,22 @@ __device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, Bwd
 // global memory, slots cleared for the next tile).  The table starts clear (table_clear once per CTA), and a
 // persistent CTA overlaps the flush of one tile with the halo load of the next.
 
-template <bool ATTR, bool EXACT>
-__device__ __forceinline__ void table_clear(BwdShared<ATTR, EXACT>& S) {
+template <int NA, bool EXACT>
+__device__ __forceinline__ void table_clear(BwdShared<NA, EXACT>& S) {
     for (int i = threadIdx.x; i < kSlots; i += kThreads) {
         S.skey[i] = -1;
         S.sval[i][0] = 0.f;
         S.sval[i][1] = 0.f;
         S.sval[i][2] = 0.f;
-        if (ATTR) {
+        if (NA > 0) {
 #pragma unroll
-            for (int j = 0; j < kMaxA; ++j) S.sattr[i][j] = 0.f;
+            for (int j = 0; j < (NA > 0 ? NA : 1); ++j) S.sattr[i][j] = 0.f;
         }
     }
 }
 
-template <bool ATTR, bool EXACT>
-__device__ __forceinline__ void tile_halo(const BItem& it, int tx, int ty, BwdShared<ATTR, EXACT>& S) {
+template <int NA, bool EXACT>
+__device__ __forceinline__ void tile_halo(const BItem& it, int tx, int ty, BwdShared<NA, EXACT>& S) {
     for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
         const int hy = i / kHW, hx = i % kHW;
         const int gx = tx * kTW + hx - 1, gy = ty * kTH + hy - 1;
@@ -291,11 +291,11 @@ __device__ __forceinline__ void tile_halo(const BItem& it, int tx, int ty, BwdSh
 }
 
 // The 32x8 tile (tx, ty) of an item, after tile_halo and a barrier.
-// ATTR: also produce the attribute gradients (channels [a0, a0 + A) of each vertex's attribute row, A <= 4:
+// NA > 0: also produce the attribute gradients (channels [a0, a0 + NA) of each vertex's attribute row, NA <= 4:
 // the interpolated channels, or (u, v) in texture mode), aggregated like the vertex gradients.
-template <bool ATTR, bool EXACT>
+template <int NA, bool EXACT>
 __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, const BwdArgs& a,
-                                             const float* __restrict__ tex, BwdShared<ATTR, EXACT>& S, void* ws) {
+                                             const float* __restrict__ tex, BwdShared<NA, EXACT>& S, void* ws) {
     const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
     const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
@@ -309,11 +309,11 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
     int t = (x < it.W && y < it.H) ? S.sidx[row + 1][lane + 1] : -1;
     int vid[3] = {0, 0, 0};
     float c0[3] = {0.f, 0.f, 0.f}, c1[3] = {0.f, 0.f, 0.f}, c2[3] = {0.f, 0.f, 0.f};  // per vertex: x, y, zeta
-    float ca[3][kMaxA];  // per vertex: attribute-gradient channels (ATTR)
+    float ca[3][NA > 0 ? NA : 1];  // per vertex: attribute-gradient channels (NA > 0)
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int j = 0; j < kMaxA; ++j) ca[k][j] = 0.f;
+        for (int j = 0; j < (NA > 0 ? NA : 1); ++j) ca[k][j] = 0.f;
     if (t >= it.T) {
         set_status(ws, kStatusRange);
         t = -1;
@@ -357,9 +357,9 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
                     D01 += gc * (a0 - a1);
                     D02 += gc * (a0 - a2);
                     D12 += gc * (a1 - a2);
-                    if (ATTR) {
+                    if (NA > 0) {
 #pragma unroll
-                        for (int j = 0; j < kMaxA; ++j)
+                        for (int j = 0; j < (NA > 0 ? NA : 1); ++j)
                             if (j == c) {
                                 ca[0][j] = b[0] * gc;
                                 ca[1][j] = b[1] * gc;
@@ -382,7 +382,7 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
                 D01 = gu * (uk[0] - uk[1]) + gv * (vk[0] - vk[1]);
                 D02 = gu * (uk[0] - uk[2]) + gv * (vk[0] - vk[2]);
                 D12 = gu * (uk[1] - uk[2]) + gv * (vk[1] - vk[2]);
-                if (ATTR) {
+                if (NA > 0) {
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         ca[k][0] = b[k] * gu;
@@ -442,7 +442,7 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
     const bool head = lane == 0 || tprev != t;
     const unsigned heads = __ballot_sync(full, head);
     const int seg = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // first lane of this run
-    const bool contributes = t >= 0 && (ATTR || c0[0] != 0.f || c1[0] != 0.f || c2[0] != 0.f || c0[1] != 0.f ||
+    const bool contributes = t >= 0 && (NA > 0 || c0[0] != 0.f || c1[0] != 0.f || c2[0] != 0.f || c0[1] != 0.f ||
                                         c1[1] != 0.f || c2[1] != 0.f || c0[2] != 0.f || c1[2] != 0.f ||
                                         c2[2] != 0.f);
     const unsigned any = __ballot_sync(full, contributes);
@@ -465,9 +465,9 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
                 c1[k] += a1_;
                 c2[k] += a2_;
             }
-            if (ATTR) {
+            if (NA > 0) {
 #pragma unroll
-                for (int j = 0; j < kMaxA; ++j) {
+                for (int j = 0; j < (NA > 0 ? NA : 1); ++j) {
                     if (j >= A) break;
                     const float aj = __shfl_up_sync(full, ca[k][j], dlt);
                     if (take) ca[k][j] += aj;
@@ -486,18 +486,18 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
                 atomicAdd(&S.sval[sl][0], c0[k]);
                 atomicAdd(&S.sval[sl][1], c1[k]);
                 atomicAdd(&S.sval[sl][2], c2[k]);
-                if (ATTR) {
+                if (NA > 0) {
 #pragma unroll
-                    for (int j = 0; j < kMaxA; ++j)
+                    for (int j = 0; j < (NA > 0 ? NA : 1); ++j)
                         if (j < A) atomicAdd(&S.sattr[sl][j], ca[k][j]);
                 }
             } else {  // table full: straight to global memory
                 atomicAdd(gvv + 3 * (size_t)vid[k], (double)c0[k]);
                 atomicAdd(gvv + 3 * (size_t)vid[k] + 1, (double)c1[k]);
                 atomicAdd(gvv + 3 * (size_t)vid[k] + 2, (double)c2[k]);
-                if (ATTR) {
+                if (NA > 0) {
 #pragma unroll
-                    for (int j = 0; j < kMaxA; ++j)
+                    for (int j = 0; j < (NA > 0 ? NA : 1); ++j)
                         if (j < A) atomicAdd(grad_attr + (size_t)vid[k] * a.sh.C_attr + a0 + j, ca[k][j]);
                 }
             }
@@ -506,8 +506,8 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
 }
 
 // After tile_compute and a barrier: add the table to global memory and clear it.
-template <bool ATTR, bool EXACT>
-__device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, BwdShared<ATTR, EXACT>& S) {
+template <int NA, bool EXACT>
+__device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, BwdShared<NA, EXACT>& S) {
     const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
     const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
     double* gvv = it.gv;
@@ -522,9 +522,9 @@ __device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, Bw
         if (s0 != 0.f) atomicAdd(gvv + 3 * (size_t)v, (double)s0);
         if (s1 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 1, (double)s1);
         if (s2 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 2, (double)s2);
-        if (ATTR) {
+        if (NA > 0) {
 #pragma unroll
-            for (int j = 0; j < kMaxA; ++j) {
+            for (int j = 0; j < (NA > 0 ? NA : 1); ++j) {
                 if (j >= A) break;
                 const float sa = S.sattr[i][j];
                 S.sattr[i][j] = 0.f;
@@ -534,14 +534,14 @@ __device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, Bw
     }
 }
 
-template <bool ATTR, bool EXACT>
+template <int NA, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
                                                        const int* __restrict__ index, const float* __restrict__ image,
                                                        const float* __restrict__ grad, const float* __restrict__ attr,
                                                        const float* __restrict__ tex, BwdArgs a,
                                                        double* __restrict__ grad_vpix, float* __restrict__ grad_attr,
                                                        void* ws) {
-    __shared__ BwdShared<ATTR, EXACT> S;
+    __shared__ BwdShared<NA, EXACT> S;
     const int tiles_per_view = a.ntx * a.nty;
     const int view = blockIdx.x / tiles_per_view;
     const int local = blockIdx.x % tiles_per_view;
@@ -559,13 +559,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __re
     table_clear(S);
     tile_halo(it, local % a.ntx, local / a.ntx, S);
     __syncthreads();
-    tile_compute<ATTR, EXACT>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
+    tile_compute<NA, EXACT>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
     __syncthreads();
     tile_flush(it, a, S);
 }
 
 // Persistent: each CTA takes the next backward tile of any item from the work queue.
-template <bool ATTR, bool EXACT>
+template <int NA, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex* __restrict__ vpix,
                                                              const int* __restrict__ tris,
                                                              const mer_item* __restrict__ items, int n_items,
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex
                                                              const float* __restrict__ tex, BwdArgs a,
                                                              double* __restrict__ grad_vpix,
                                                              float* __restrict__ grad_attr, void* ws) {
-    __shared__ BwdShared<ATTR, EXACT> S;
+    __shared__ BwdShared<NA, EXACT> S;
     __shared__ long long s_tile;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     const int C = a.sh.C, Ca = a.sh.C_attr;
@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex
         tile_halo(it, tx, ty, S);
         __syncthreads();
         if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_backward, 1ull);
-        tile_compute<ATTR, EXACT>(it, tx, ty, a, tex, S, ws);
+        tile_compute<NA, EXACT>(it, tx, ty, a, tex, S, ws);
         __syncthreads();
         tile_flush(it, a, S);
     }
@@ -624,6 +624,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex
 }  // namespace mer
 
 using namespace mer;
+
+namespace {
+// Attribute-gradient channels a launch carries (0 without attribute gradients): the interpolated channels,
+// or (u, v) in texture mode.
+int attr_channels(const mer_shading* sh, const float* grad_attr) {
+    if (!grad_attr) return 0;
+    const int A = sh->uv_offset < 0 ? sh->n_main : 2;
+    return A >= 1 && A <= kMaxA ? A : -1;
+}
+}  // namespace
 
 extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
                                          long long btiles, const int* index, const float* image,
@@ -644,7 +654,7 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
         int per_sm = 0, sms = 0, dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 2;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 2;
-        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_batch<false, false>,
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_batch<0, false>,
                                                                             kThreads, 0);
         if (e != cudaSuccess) return 2;
         grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
@@ -653,10 +663,18 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
 #define MER_BWD_BATCH(A, E)                                                                                        \
     k_backward_batch<A, E><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, image, grad_image, \
                                                      attr, tex, a, grad_vpix, grad_attr, ws)
-    if (grad_attr) {
-        if (exact) MER_BWD_BATCH(true, true); else MER_BWD_BATCH(true, false);
-    } else {
-        if (exact) MER_BWD_BATCH(false, true); else MER_BWD_BATCH(false, false);
+    switch (attr_channels(sh, grad_attr) * 2 + (exact ? 1 : 0)) {
+        case 0: MER_BWD_BATCH(0, false); break;
+        case 1: MER_BWD_BATCH(0, true); break;
+        case 2: MER_BWD_BATCH(1, false); break;
+        case 3: MER_BWD_BATCH(1, true); break;
+        case 4: MER_BWD_BATCH(2, false); break;
+        case 5: MER_BWD_BATCH(2, true); break;
+        case 6: MER_BWD_BATCH(3, false); break;
+        case 7: MER_BWD_BATCH(3, true); break;
+        case 8: MER_BWD_BATCH(4, false); break;
+        case 9: MER_BWD_BATCH(4, true); break;
+        default: return 1;
     }
 #undef MER_BWD_BATCH
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
@@ -680,10 +698,18 @@ extern "C" int mer_launch_backward(const mer_vertex* vpix, int V, const int* tri
 #define MER_BWD(A, E)                                                                                             \
     k_backward<A, E><<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, image, grad_image, attr, tex, a,     \
                                                            grad_vpix, grad_attr, ws)
-    if (grad_attr) {
-        if (exact) MER_BWD(true, true); else MER_BWD(true, false);
-    } else {
-        if (exact) MER_BWD(false, true); else MER_BWD(false, false);
+    switch (attr_channels(sh, grad_attr) * 2 + (exact ? 1 : 0)) {
+        case 0: MER_BWD(0, false); break;
+        case 1: MER_BWD(0, true); break;
+        case 2: MER_BWD(1, false); break;
+        case 3: MER_BWD(1, true); break;
+        case 4: MER_BWD(2, false); break;
+        case 5: MER_BWD(2, true); break;
+        case 6: MER_BWD(3, false); break;
+        case 7: MER_BWD(3, true); break;
+        case 8: MER_BWD(4, false); break;
+        case 9: MER_BWD(4, true); break;
+        default: return 1;
     }
 #undef MER_BWD
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
