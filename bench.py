@@ -108,12 +108,12 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_backward_batch launch, from an ncu capture
-# of the same workload at 4 views (inputs already larger than L2), per pixel of the launch, with the sha256 of
-# the kernel's sources it was taken on: a launch of n views moves n*H*W times this.  It is reported only while
-# the sources are unchanged.
-BACKWARD_TRAFFIC = {"bytes_per_pixel": 22.9189,
-                    "sources_sha256": "d0e4bb5679b1e4a65be8b67edbae6502ea7fe6f33fe64f65871dac21f04f55bc",
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) and warp instructions (smsp__inst_executed.sum) of
+# one k_backward_batch launch, from an ncu capture of the same workload at 4 views (inputs already larger than
+# L2), per pixel of the launch, with the sha256 of the kernel's sources they were taken on: a launch of n views
+# moves / issues n*H*W times these.  They are reported only while the sources are unchanged.
+BACKWARD_TRAFFIC = {"bytes_per_pixel": 22.9364, "warp_instructions_per_pixel": 46.9457,
+                    "sources_sha256": "853c050d5ddf23b02efb783446f4d06ccc5b59812878866aa339f1d59b9a7957",
                     "profile": "profiles/ncu_k_backward_batch_head_4x1334x2048.md"}
 
 
@@ -132,6 +132,36 @@ def backward_traffic(pixels: int):
     if t["bytes_per_pixel"] is None or t["sources_sha256"] != backward_sources_sha256():
         return None
     return t["bytes_per_pixel"] * pixels
+
+
+def issue_peak() -> float:
+    """Warp instructions per second the SMs can issue: one per scheduler (4 per SM) per cycle at the GPU's
+    maximum SM clock."""
+    import torch
+
+    props = torch.cuda.get_device_properties(0)
+    mhz = 2070.0
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=10).stdout.split()
+        mhz = float(out[0])
+    except Exception:
+        pass
+    return props.multi_processor_count * 4 * mhz * 1e6
+
+
+def backward_issue_roofline(pixels: int, kernel_ms: float):
+    """Second roofline of the backward: warp instructions per launch (ncu count per pixel x pixels, null once
+    the sources changed) over the issue peak."""
+    t = BACKWARD_TRAFFIC
+    if t.get("warp_instructions_per_pixel") is None or t["sources_sha256"] != backward_sources_sha256():
+        return None
+    inst = t["warp_instructions_per_pixel"] * pixels
+    peak = issue_peak()
+    achieved = inst / (kernel_ms * 1e-3)
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "instructions": inst,
+            "peak_kind": "derived: SMs x 4 schedulers x 1 instruction per cycle x max SM clock"}
 
 
 def backward_bytes_per_launch(n, H, W, C, V):
@@ -487,6 +517,7 @@ def main():
         "roofline": {"bound": "hbm", "kernel": "k_backward_batch (fused edge + interior)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": backward_traffic(n * H * W),
                      "peak_kind": peak_kind, "kernel_ms": kms["bwd"], "algorithmic_bytes": bb},
+        "roofline_issue": backward_issue_roofline(n * H * W, kms["bwd"]),
         "kernels_ms": {"forward (project+raster+shade)": kms["fwd"], "bin+raster+shade (fused)": kms["rast"],
                        "backward": kms["bwd"]},
         "step_algorithmic_gbs": step_bytes(n, H, W, C, V, T, tex.numel() * 4) / (ms * 1e-3) / 1e9,
