@@ -281,13 +281,18 @@ __device__ __forceinline__ void table_clear(BwdShared<NA, EXACT>& S) {
     }
 }
 
+// Returns whether this thread loaded a covered pixel of the tile itself (not the halo).
 template <int NA, bool EXACT>
-__device__ __forceinline__ void tile_halo(const BItem& it, int tx, int ty, BwdShared<NA, EXACT>& S) {
+__device__ __forceinline__ bool tile_halo(const BItem& it, int tx, int ty, BwdShared<NA, EXACT>& S) {
+    bool covered = false;
     for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
         const int hy = i / kHW, hx = i % kHW;
         const int gx = tx * kTW + hx - 1, gy = ty * kTH + hy - 1;
-        S.sidx[hy][hx] = (gx >= 0 && gx < it.W && gy >= 0 && gy < it.H) ? __ldg(it.index + (size_t)gy * it.W + gx) : -2;
+        const int v = (gx >= 0 && gx < it.W && gy >= 0 && gy < it.H) ? __ldg(it.index + (size_t)gy * it.W + gx) : -2;
+        S.sidx[hy][hx] = v;
+        covered |= v >= 0 && hy >= 1 && hy <= kTH && hx >= 1 && hx <= kTW;
     }
+    return covered;
 }
 
 // The 32x8 tile (tx, ty) of an item, after tile_halo and a barrier.
@@ -307,6 +312,7 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
     const float* attr = it.attr;
     float* grad_attr = it.gattr;
     int t = (x < it.W && y < it.H) ? S.sidx[row + 1][lane + 1] : -1;
+    if (!__any_sync(0xffffffffu, t >= 0)) return;  // background row: no fragment, no pair
     int vid[3] = {0, 0, 0};
     float c0[3] = {0.f, 0.f, 0.f}, c1[3] = {0.f, 0.f, 0.f}, c2[3] = {0.f, 0.f, 0.f};  // per vertex: x, y, zeta
     float ca[3][NA > 0 ? NA : 1];  // per vertex: attribute-gradient channels (NA > 0)
@@ -448,9 +454,7 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
     const unsigned any = __ballot_sync(full, contributes);
     // longest run in the warp decides how many doubling steps the scan needs
     const int runlen = t >= 0 ? lane - seg + 1 : 0;  // runs of background lanes carry nothing
-    int maxrun = runlen;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxrun = max(maxrun, __shfl_xor_sync(full, maxrun, o));
+    const int maxrun = (int)__reduce_max_sync(full, (unsigned)runlen);
 #pragma unroll
     for (int dlt = 1; dlt < 32; dlt <<= 1) {
         if (!any || dlt >= maxrun) break;
@@ -557,8 +561,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __re
     it.gattr = grad_attr;
     it.V = a.V; it.T = a.T; it.H = a.H; it.W = a.W;
     table_clear(S);
-    tile_halo(it, local % a.ntx, local / a.ntx, S);
-    __syncthreads();
+    const bool covered = tile_halo(it, local % a.ntx, local / a.ntx, S);
+    if (!__syncthreads_or(covered)) return;  // background tile
     tile_compute<NA, EXACT>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
     __syncthreads();
     tile_flush(it, a, S);
@@ -585,7 +589,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex
     __syncthreads();
     // Per tile two barriers: after the halo load (thread 0 then takes the next tile id) and before the flush
     // (the next id is visible after it).  The flush of a tile and the halo load of the next touch disjoint
-    // shared memory, and the next tile's table inserts come only after its first barrier.
+    // shared memory, and the next tile's table inserts come only after its first barrier.  (A background row
+    // leaves tile_compute at once; skipping whole background tiles here instead costs registers.)
     int cur = 0;                       // item of the previous tile and its tile range [lo, hi)
     long long lo = 0, hi = 0;
     while (true) {
