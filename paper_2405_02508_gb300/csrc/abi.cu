@@ -228,7 +228,7 @@ int mer_batch_plan(mer_item* items, int n_items, int tile, mer_batch_totals* tot
         trec += m.T;
         pix += (int64_t)m.H * m.W;
         tiles += (int64_t)((m.W + tile - 1) / tile) * ((m.H + tile - 1) / tile);
-        btiles += (int64_t)((m.W + 31) / 32) * ((m.H + 7) / 8);
+        btiles += (int64_t)((m.W + mer::kBwdTileW - 1) / mer::kBwdTileW) * ((m.H + mer::kBwdTileH - 1) / mer::kBwdTileH);
     }
     const int64_t lim = (int64_t)1 << 31;
     if (vrec >= lim || trec >= lim || pix >= lim || tiles >= lim || btiles >= lim) return MER_EINVAL;

@@ -1,7 +1,7 @@
 // backward.cu -- EdgeGrad module backward (Sec. 4.2-4.4, Supp. A.2-A.3) fused with
 // the interior term Omega (Eq. 5) and the interpolation / barycentrics backward.
 //
-// One CTA per 32x8 pixel tile of one view (a warp = one row of 32 pixels); the
+// One CTA per 32x16 pixel tile of one view (a warp = two rows of 32 pixels); the
 // tile's index image plus a one-pixel halo sits in shared memory.  Each covered
 // pixel p owns the fragment of its triangle t at its centre and accumulates that
 // fragment's gradient dL/dr (a 3-vector in x_s, y_s, zeta):
@@ -23,9 +23,11 @@
 
 namespace mer {
 
-constexpr int kTW = 32, kTH = 8;  // tile: 8 warps, one row each
+constexpr int kTW = kBwdTileW, kTH = kBwdTileH;  // tile: 8 warps, two rows each
+constexpr int kRows = 2;                          // rows per warp
 constexpr int kHW = kTW + 2, kHH = kTH + 2;
-constexpr int kThreads = kTW * kTH;
+constexpr int kThreads = 256;
+static_assert(kTW == 32 && kTH == kRows * kThreads / 32, "a warp spans the tile's width");
 constexpr int kSlots = 512;       // per-tile vertex table (a tile touches ~10-50 vertices)
 
 struct BwdArgs {
@@ -99,72 +101,89 @@ struct BwdShared {
     int skey[kSlots];
     float sval[kSlots][3];
     float sattr[NA > 0 ? kSlots : 1][NA > 0 ? NA : 1];
-    float efrag[kTH][32][3];  // per warp: edge-term fragment gradients returned to the pixel's lane
+    float efrag[kTH][32][3];  // per row: edge-term fragment gradients returned to the pixel's lane
     float evert[EXACT ? kTH : 1][32][3][2];  // exact-crossing option: per pixel, (x, y) per triangle vertex
 };
 
-// Edge term of the warp's row (all 32 lanes call it together).  Lane l owns the fragment of pixel (x0 + l, y)
-// and its triangle t (vertex ids vid, snapped X, Y).  The (pixel, neighbour) pairs whose ids differ are
-// compacted into one list per warp and classified 32 at a time, every lane busy, the source pixel's triangle
-// taken from its lane by shuffle; a pair that scatters to the source fragment adds into that pixel's slot of a
-// per-warp shared buffer, which the owning lane finally adds to (fx, fy, fz).
+// Edge term of the warp's rows r0 .. r0 + kRows - 1, before their per-pixel pass (all 32 lanes call it
+// together).  The (pixel, neighbour) pairs whose ids differ, with the pixel covered, are compacted into one
+// list for the warp's rows (most rows hold far fewer than 32 such pairs, so the rows share passes) and
+// classified 32 at a time; a pair whose source fragment scatters adds into that pixel's slot of the per-row
+// shared buffer efrag (evert for the exact-crossing option), read back by the pixel's lane in its row pass.
+// Returns false when the rows hold no pair (the buffers are then not written).
 template <int NA, bool EXACT>
-__device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, BwdShared<NA, EXACT>& S, void* ws, int row,
-                                          int lane, int x, int y, int t, const int vid[3], const int X[3],
-                                          const int Y[3], float& fx, float& fy, float& fz) {
+__device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, BwdShared<NA, EXACT>& S, void* ws,
+                                          int r0, int lane, int x0, int y0) {
     const unsigned full = 0xffffffffu;
     const int C = a.sh.C;
-    unsigned m[4];
+    constexpr int kM = 4 * kRows;
+    unsigned m[kM];  // per (row k, direction d): lanes whose pixel is covered and whose neighbour in d differs
+    int np[kM + 1];  // prefix counts
+    np[0] = 0;
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
-        const int ddy = d == 2 ? -1 : (d == 3 ? 1 : 0);
-        const int tq = S.sidx[row + 1 + ddy][lane + 1 + ddx];
-        m[d] = __ballot_sync(full, t >= 0 && tq != t && tq != -2);
+    for (int k = 0; k < kRows; ++k) {
+        const int row = r0 + k;
+        const int t = S.sidx[row + 1][lane + 1];  // -2 outside the image
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
+            const int ddy = d == 2 ? -1 : (d == 3 ? 1 : 0);
+            const int tq = S.sidx[row + 1 + ddy][lane + 1 + ddx];
+            m[4 * k + d] = __ballot_sync(full, t >= 0 && tq != t && tq != -2);
+            np[4 * k + d + 1] = np[4 * k + d] + __popc(m[4 * k + d]);
+        }
     }
-    const int n0 = __popc(m[0]), n1 = n0 + __popc(m[1]), n2 = n1 + __popc(m[2]), n = n2 + __popc(m[3]);
-    if (n == 0) {
+    const int n = np[kM];
+    if (n == 0) return false;
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+        float* acc = &S.efrag[r0 + k][lane][0];
+        acc[0] = 0.f;
+        acc[1] = 0.f;
+        acc[2] = 0.f;
         if (EXACT) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                S.evert[row][lane][k][0] = 0.f;
-                S.evert[row][lane][k][1] = 0.f;
+            for (int v = 0; v < 3; ++v) {
+                S.evert[r0 + k][lane][v][0] = 0.f;
+                S.evert[r0 + k][lane][v][1] = 0.f;
             }
-        }
-        return;
-    }
-    float* acc = &S.efrag[row][0][0];
-    acc[3 * lane] = 0.f;
-    acc[3 * lane + 1] = 0.f;
-    acc[3 * lane + 2] = 0.f;
-    if (EXACT) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            S.evert[row][lane][k][0] = 0.f;
-            S.evert[row][lane][k][1] = 0.f;
         }
     }
     __syncwarp();
-    const int x0 = x - lane;
     const mer_vertex* vb = it.vb;
-    for (int base = 0; base < n; base += 32) {
-        const int i = base + lane;
-        const int d = i < n0 ? 0 : (i < n1 ? 1 : (i < n2 ? 2 : 3));
-        const int r = i - (d == 0 ? 0 : (d == 1 ? n0 : (d == 2 ? n1 : n2)));
-        const unsigned md = d == 0 ? m[0] : (d == 1 ? m[1] : (d == 2 ? m[2] : m[3]));
-        const int src = i < n ? (int)__fns(md, 0, r + 1) : lane;
-        int vs[3], Xs[3], Ys[3];
+    for (int i = lane; i < n; i += 32) {
+        // list entry i -> mask s (the last one whose prefix count is <= i), its row, direction and source lane
+        int s = 0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            vs[k] = __shfl_sync(full, vid[k], src);
-            Xs[k] = __shfl_sync(full, X[k], src);
-            Ys[k] = __shfl_sync(full, Y[k], src);
-        }
-        if (i >= n) continue;
+        for (int j = 1; j < kM; ++j)
+            if (i >= np[j]) s = j;
+        unsigned md = m[0];
+        int start = 0;
+#pragma unroll
+        for (int j = 1; j < kM; ++j)
+            if (s == j) {
+                md = m[j];
+                start = np[j];
+            }
+        const int row = r0 + (s >> 2), d = s & 3;
+        const int src = (int)__fns(md, 0, i - start + 1);
         const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
         const int ddy = d == 2 ? -1 : (d == 3 ? 1 : 0);
-        const int px = x0 + src;
+        const int px = x0 + src, y = y0 + row;
+        const int ts = S.sidx[row + 1][src + 1];
         const int tq = S.sidx[row + 1 + ddy][src + 1 + ddx];
+        int vs[3];
+        if (ts >= it.T || !tri_ids(it.tris, ts, it.V, vs)) {
+            set_status(ws, kStatusRange);
+            continue;
+        }
+        int Xs[3], Ys[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vs[k]));
+            Xs[k] = xy.x;
+            Ys[k] = xy.y;
+        }
         const int qx = px + ddx, qy = y + ddy;
         const int axis = ddx != 0 ? 0 : 1;
         bool inter = false;
@@ -252,14 +271,13 @@ __device__ __forceinline__ void edge_term(const BItem& it, const BwdArgs& a, Bwd
             if (axis == 0) ex = kk * nv0; else ey = kk * nv0;
             ez = kk * nv1;
         }
-        atomicAdd(acc + 3 * src, ex);
-        atomicAdd(acc + 3 * src + 1, ey);
-        atomicAdd(acc + 3 * src + 2, ez);
+        float* acc = &S.efrag[row][src][0];
+        if (ex != 0.f) atomicAdd(acc, ex);
+        if (ey != 0.f) atomicAdd(acc + 1, ey);
+        if (ez != 0.f) atomicAdd(acc + 2, ez);
     }
     __syncwarp();
-    fx += acc[3 * lane];
-    fy += acc[3 * lane + 1];
-    fz += acc[3 * lane + 2];
+    return true;
 }
 
 // A tile's work is split in three phases separated by CTA barriers: tile_halo (index tile + halo into shared
@@ -295,15 +313,16 @@ __device__ __forceinline__ bool tile_halo(const BItem& it, int tx, int ty, BwdSh
     return covered;
 }
 
-// The 32x8 tile (tx, ty) of an item, after tile_halo and a barrier.
+// Per-pixel pass of row `row` of the tile (tx, ty) of an item, after its edge_rows (pairs: whether that wrote
+// the row's edge buffers).
 // NA > 0: also produce the attribute gradients (channels [a0, a0 + NA) of each vertex's attribute row, NA <= 4:
 // the interpolated channels, or (u, v) in texture mode), aggregated like the vertex gradients.
 template <int NA, bool EXACT>
-__device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, const BwdArgs& a,
-                                             const float* __restrict__ tex, BwdShared<NA, EXACT>& S, void* ws) {
+__device__ __forceinline__ void row_pass(const BItem& it, int tx, int ty, int row, int lane, bool pairs,
+                                         const BwdArgs& a, const float* __restrict__ tex, BwdShared<NA, EXACT>& S,
+                                         void* ws) {
     const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
     const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
-    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
     const int x = tx * kTW + lane, y = ty * kTH + row;
     const int C = a.sh.C;
     const mer_vertex* vb = it.vb;
@@ -330,18 +349,13 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
     }
     float fx = 0.f, fy = 0.f, fz = 0.f;
     float hz[3] = {0.f, 0.f, 0.f}, lam[3] = {0.f, 0.f, 0.f};
-    int X[3] = {0, 0, 0}, Y[3] = {0, 0, 0};
     if (t >= 0) {
         const size_t p = (size_t)y * it.W + x;
         const float* gp = grad + p * C;
         const VRec rv[3] = {load_vrec(vb + vid[0]), load_vrec(vb + vid[1]), load_vrec(vb + vid[2])};
         const Bary B = screen_bary(rv, x, y);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            lam[k] = B.lam[k];
-            X[k] = rv[k].X;
-            Y[k] = rv[k].Y;
-        }
+        for (int k = 0; k < 3; ++k) lam[k] = B.lam[k];
 
         if (a.terms & MER_INTERIOR) {
             const float z[3] = {rv[0].zeta, rv[1].zeta, rv[2].zeta};
@@ -422,8 +436,10 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
 
     }
 
-    if (a.terms & MER_EDGE) {
-        edge_term(it, a, S, ws, row, lane, x, y, t, vid, X, Y, fx, fy, fz);
+    if (pairs && t >= 0) {  // the edge term of the pixel's fragment, from edge_rows
+        fx += S.efrag[row][lane][0];
+        fy += S.efrag[row][lane][1];
+        fz += S.efrag[row][lane][2];
     }
     if (t >= 0) {
 #pragma unroll
@@ -433,7 +449,7 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
             c1[k] = l * fy;
             c2[k] = l * (fz + hz[k]);
         }
-        if (EXACT && (a.terms & MER_EDGE)) {  // the exact-crossing parts, already split per vertex
+        if (EXACT && pairs) {  // the exact-crossing parts, already split per vertex
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 c0[k] += S.evert[row][lane][k][0];
@@ -507,6 +523,17 @@ __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, co
             }
         }
     }
+}
+
+// The tile (tx, ty) of an item, after tile_halo and a barrier: each warp takes rows kRows * warp ..
+// kRows * warp + kRows - 1, first their edge pairs together, then each row's pixels.
+template <int NA, bool EXACT>
+__device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, const BwdArgs& a,
+                                             const float* __restrict__ tex, BwdShared<NA, EXACT>& S, void* ws) {
+    const int lane = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * kRows;
+    const bool pairs = (a.terms & MER_EDGE) && edge_rows<NA, EXACT>(it, a, S, ws, r0, lane, tx * kTW, ty * kTH);
+#pragma unroll 1
+    for (int k = 0; k < kRows; ++k) row_pass<NA, EXACT>(it, tx, ty, r0 + k, lane, pairs, a, tex, S, ws);
 }
 
 // After tile_compute and a barrier: add the table to global memory and clear it.

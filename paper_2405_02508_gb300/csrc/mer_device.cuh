@@ -30,6 +30,9 @@ static_assert(sizeof(WsHeader) == 256, "header");
 constexpr int kStatusOverflow = 1;
 constexpr int kStatusRange = 2;
 
+// Backward tile: 32 x 16 pixels, one CTA of 8 warps (two rows each); the batch plan counts items in these.
+constexpr int kBwdTileW = 32, kBwdTileH = 16;
+
 // Per (view, triangle) raster record written by the binning pass, 64 bytes.
 struct TriRaster {
     int X[3], Y[3];   // snapped vertex positions

@@ -66,8 +66,8 @@ def test_batch_plan_offsets():
     assert [arr[k].trec for k in range(3)] == [0, 7, 7]
     assert [arr[k].pix for k in range(3)] == [0, 2000, 2000]
     assert [arr[k].tile for k in range(3)] == [0, 4, 4]  # ceil(50/32) * ceil(40/32) = 4
-    assert [arr[k].btile for k in range(3)] == [0, 10, 10]  # ceil(50/32) * ceil(40/8) = 10
-    assert (tot.vrecs, tot.trecs, tot.pixels, tot.tiles, tot.btiles) == (15, 10, 2000 + 561, 4 + 2, 10 + 6)
+    assert [arr[k].btile for k in range(3)] == [0, 6, 6]  # backward tiles of 32 x 16: ceil(50/32) * ceil(40/16)
+    assert (tot.vrecs, tot.trecs, tot.pixels, tot.tiles, tot.btiles) == (15, 10, 2000 + 561, 4 + 2, 6 + 4)
     assert binding.mer_batch_workspace_size(tot) > 0
     arr[0].H = 9000
     import pytest
