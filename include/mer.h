@@ -257,8 +257,9 @@ int mer_batch_plan(mer_item* items, int n_items, int tile, mer_batch_totals* tot
 size_t mer_batch_workspace_size(const mer_batch_totals* totals, int64_t bin_capacity);
 
 /* Batched counterparts of the calls above; `items` is the planned table in device memory, `totals`
- * a host pointer.  persistent_ctas: CTAs of the persistent raster and backward (0 = as many as fit
- * on the device at once). */
+ * a host pointer.  persistent_ctas: CTAs (of 256 threads) of the persistent raster, which keeps 4 per SM
+ * resident; the persistent backward, which keeps 5 per SM, launches persistent_ctas * 5 / 4 of its own
+ * (0 = as many as fit on the device at once, for either). */
 int mer_batch_project(const float* verts, const mer_camera* cams, const mer_item* items,
                       const mer_batch_totals* totals, mer_vertex* vpix, void* stream);
 int mer_batch_rasterize(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,

@@ -11,10 +11,12 @@
 //     pair (oriented left->right / top->bottom), then the Sec. 4.3 rule (p on
 //     top -> dp/dr = 1 on the pair axis) or Eq. 12 (intersection) for p's side.
 // The fragment gradient is gathered to the 3 vertices with p's screen
-// barycentrics (dL/dv_i = lambda_i dL/dr).  The 9 per-pixel vertex terms are
-// summed first over each run of equal triangle id in the warp's row (segmented
-// shuffle scan, FP32), then per vertex in a shared-memory table (FP32), and the
-// tile's per-vertex totals go to grad_vpix with one FP64 atomic per component.
+// barycentrics (dL/dv_i = lambda_i dL/dr).  A warp first classifies the edge
+// pairs of both its rows together (they rarely fill more than one 32-lane pass),
+// then takes its rows one at a time: the 9 per-pixel vertex terms are summed over
+// each run of equal triangle id in the row (segmented shuffle scan, FP32), then
+// per vertex in a shared-memory table (FP32), and the tile's per-vertex totals go
+// to grad_vpix with one FP64 atomic per component.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -27,8 +29,9 @@ constexpr int kTW = kBwdTileW, kTH = kBwdTileH;  // tile: 8 warps, two rows each
 constexpr int kRows = 2;                          // rows per warp
 constexpr int kHW = kTW + 2, kHH = kTH + 2;
 constexpr int kThreads = 256;
+constexpr int kCtasPerSm = 5;                     // resident CTAs per SM: at most 51 registers a thread
 static_assert(kTW == 32 && kTH == kRows * kThreads / 32, "a warp spans the tile's width");
-constexpr int kSlots = 512;       // per-tile vertex table (a tile touches ~10-50 vertices)
+constexpr int kSlots = 512;       // per-tile vertex table (a 32x16 tile touches ~20-100 vertices)
 
 struct BwdArgs {
     mer_shading sh;
@@ -566,7 +569,7 @@ __device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, Bw
 }
 
 template <int NA, bool EXACT>
-__global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
                                                        const int* __restrict__ index, const float* __restrict__ image,
                                                        const float* __restrict__ grad, const float* __restrict__ attr,
                                                        const float* __restrict__ tex, BwdArgs a,
@@ -597,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_backward(const mer_vertex* __re
 
 // Persistent: each CTA takes the next backward tile of any item from the work queue.
 template <int NA, bool EXACT>
-__global__ void __launch_bounds__(kThreads, 4) k_backward_batch(const mer_vertex* __restrict__ vpix,
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward_batch(const mer_vertex* __restrict__ vpix,
                                                              const int* __restrict__ tris,
                                                              const mer_item* __restrict__ items, int n_items,
                                                              long long btiles, const int* __restrict__ index,
@@ -681,7 +684,8 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
     a.tex_vec4 = a.tex_stride == 4 && tex && (reinterpret_cast<uintptr_t>(tex) & 15u) == 0;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     if (cudaMemsetAsync(&hdr->queue_backward, 0, sizeof(unsigned long long), s) != cudaSuccess) return 2;
-    unsigned grid = persistent_ctas > 0 ? (unsigned)persistent_ctas : 0u;
+    // persistent_ctas sizes the raster's grid (4 resident CTAs per SM); the backward keeps as many waves
+    unsigned grid = persistent_ctas > 0 ? (unsigned)((long long)persistent_ctas * kCtasPerSm / 4) : 0u;
     if (grid == 0) {
         int per_sm = 0, sms = 0, dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 2;
