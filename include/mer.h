@@ -258,7 +258,7 @@ size_t mer_batch_workspace_size(const mer_batch_totals* totals, int64_t bin_capa
 
 /* Batched counterparts of the calls above; `items` is the planned table in device memory, `totals`
  * a host pointer.  persistent_ctas: CTAs (of 256 threads) of the persistent raster, which keeps 4 per SM
- * resident; the persistent backward, which keeps 5 per SM, launches persistent_ctas * 5 / 4 of its own
+ * resident; the persistent backward, which keeps 6 per SM, launches persistent_ctas * 6 / 4 of its own
  * (0 = as many as fit on the device at once, for either). */
 int mer_batch_project(const float* verts, const mer_camera* cams, const mer_item* items,
                       const mer_batch_totals* totals, mer_vertex* vpix, void* stream);

@@ -173,7 +173,7 @@ class PlainRenderer:
 
 def default_persistent_ctas() -> int:
     """Persistent grid: the number of raster CTAs that fit on the device at once (4 per SM; the backward
-    scales it to its own 5 per SM)."""
+    scales it to its own 6 per SM)."""
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     return int(props.multi_processor_count) * 4
 

@@ -29,7 +29,7 @@ constexpr int kTW = kBwdTileW, kTH = kBwdTileH;  // tile: 8 warps, two rows each
 constexpr int kRows = 2;                          // rows per warp
 constexpr int kHW = kTW + 2, kHH = kTH + 2;
 constexpr int kThreads = 256;
-constexpr int kCtasPerSm = 5;                     // resident CTAs per SM: at most 51 registers a thread
+constexpr int kCtasPerSm = 6;                     // resident CTAs per SM: at most 42 registers a thread
 static_assert(kTW == 32 && kTH == kRows * kThreads / 32, "a warp spans the tile's width");
 constexpr int kSlots = 512;       // per-tile vertex table (a 32x16 tile touches ~20-100 vertices)
 
