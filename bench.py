@@ -453,14 +453,14 @@ def main():
         B.mer_batch_project(verts, br.cams, br.items, br.tot, br.vpix)
         ev["rast"][2 * i].record(stream)
         B.mer_batch_render(br.vpix, br.tris, br.items, br.tot, br.workspace, br.index, attr, tex, br.bg, br.sh,
-                           br.image, None, None, br.persistent_ctas)
+                           br.image, None, None, br.persistent_ctas, br.cover)
         ev["rast"][2 * i + 1].record(stream)
         ev["fwd"][2 * i + 1].record(stream)
         br.grad_vpix.zero_()
         br.grad_verts.zero_()
         ev["bwd"][2 * i].record(stream)
         B.mer_batch_backward(br.vpix, br.tris, br.items, br.tot, br.index, br.image, g, attr, tex, br.sh, 7,
-                             br.grad_vpix, None, br.workspace, br.persistent_ctas)
+                             br.grad_vpix, None, br.workspace, br.persistent_ctas, br.cover)
         ev["bwd"][2 * i + 1].record(stream)
         B.mer_batch_project_backward(br.cams, br.items, br.tot, br.vpix, br.grad_vpix, br.grad_verts)
     torch.cuda.synchronize()

@@ -107,6 +107,26 @@ enum {
                               instead of the foreground fragment's barycentrics */
 };
 
+/* Bits of the optional cover image [n,H,W] uint8 that the rasterizers write beside the index image.  It
+ * records which triangles cover each pixel centre, as far as the backward pass needs it to skip pixel pairs
+ * that cannot scatter: an edge pair (p, q) with triangles t_p != t_q scatters into p's fragment only if t_q
+ * covers p's centre too (Sec. 4.3: p on top of t_q, or an intersection), so when no second triangle of
+ * t_q's facing covers p, the pair's classification is known without loading either triangle.  This is an
+ * implementation aid of this library; the paper has no counterpart and the results do not change.
+ * Facing: "front" = negative snapped area (y down: counter-clockwise on screen), "back" = positive.
+ * The counts leave out back-facing triangles that lie behind the whole bin tile (the raster skips them);
+ * such a triangle wins no pixel of that tile, so the counts are exact for pairs inside one bin tile, and a
+ * pair from a pixel across the border of its bin tile is always classified in full (the border bits). */
+enum {
+    MER_COVER_SAME_2 = 1,       /* another triangle with the visible triangle's facing covers the centre */
+    MER_COVER_OTHER_1 = 2,      /* a triangle with the other facing covers the centre */
+    MER_COVER_WINNER_BACK = 4,  /* the visible triangle (the index) is back-facing */
+    MER_COVER_BORDER_L = 8,     /* first column of its bin tile (the pair to the left crosses the border) */
+    MER_COVER_BORDER_R = 16,    /* last column */
+    MER_COVER_BORDER_T = 32,    /* first row */
+    MER_COVER_BORDER_B = 64     /* last row */
+};
+
 const char* mer_strerror(int code);
 int mer_version(void);
 
@@ -135,10 +155,12 @@ int mer_project_screen(const double* scr, int V, int n, mer_vertex* vpix, void* 
  * functions E_i = cross(v_j - P, v_k - P) of the snapped positions (s = sign of
  * the area; both windings drawn), or E_i == 0 on a top-left edge.  Depth test:
  * largest zeta_test = sum_i E_i zeta_i / sum_i E_i, ties to the lower id.
- * The workspace keeps the bins; its contents are not needed afterwards. */
+ * The workspace keeps the bins; its contents are not needed afterwards.
+ * cover [n,H,W] uint8 or NULL: the MER_COVER_* bits of every pixel (background pixels: only the border
+ * bits), to pass to mer_backward with this index image. */
 int mer_rasterize(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
                   int tile, void* workspace, size_t workspace_bytes,
-                  int32_t* index, float* depth, float* bary, void* stream);
+                  int32_t* index, float* depth, float* bary, uint8_t* cover, void* stream);
 /* mer_project followed by mer_rasterize: world-space vertices [V,3] and n cameras in, index / depth /
  * bary out, the projected records written to vpix [n,V] (the other calls take them).  Arguments, errors and
  * workspace as the two calls. */
@@ -193,9 +215,13 @@ int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, 
  * arithmetic is FP32; the sums over pixels are accumulated in FP64 because a
  * vertex gradient component can be a strongly cancelling sum of many terms.
  * grad_attr [V,C_attr] (+=) or NULL: dL/d(attr) of the interior term (interpolation mode: at most 4
- * interpolated channels; texture mode: the u, v columns). */
+ * interpolated channels; texture mode: the u, v columns).
+ * cover [n,H,W] uint8 or NULL: the cover image the rasterizer wrote with this index image.  With it,
+ * pairs whose neighbour triangle cannot cover the pixel centre (see MER_COVER_*) are not classified;
+ * the results are the same as without it.  A cover image that does not belong to `index` can drop
+ * scattering pairs (no memory fault). */
 int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
-                 const int32_t* index, const float* image, const float* grad_image,
+                 const int32_t* index, const uint8_t* cover, const float* image, const float* grad_image,
                  const float* attr, const float* tex, const mer_shading* shading_host, int terms,
                  double* grad_vpix, float* grad_attr, void* status_ws, void* stream);
 
@@ -264,7 +290,8 @@ int mer_batch_project(const float* verts, const mer_camera* cams, const mer_item
                       const mer_batch_totals* totals, mer_vertex* vpix, void* stream);
 int mer_batch_rasterize(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,
                         const mer_batch_totals* totals, void* workspace, size_t workspace_bytes,
-                        int32_t* index, float* depth, float* bary, int persistent_ctas, void* stream);
+                        int32_t* index, float* depth, float* bary, uint8_t* cover, int persistent_ctas,
+                        void* stream);
 int mer_batch_shade(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,
                     const mer_batch_totals* totals, const int32_t* index, const float* attr, const float* tex,
                     const float* bg_host, const mer_shading* shading_host, float* image, void* status_ws,
@@ -276,11 +303,14 @@ int mer_batch_shade(const mer_vertex* vpix, const int32_t* tris, const mer_item*
  * interpolation modules. */
 int mer_batch_render(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,
                      const mer_batch_totals* totals, void* workspace, size_t workspace_bytes,
-                     int32_t* index, float* depth, float* bary, const float* attr, const float* tex,
-                     const float* bg_host, const mer_shading* shading_host, float* image, int persistent_ctas,
-                     void* stream);
+                     int32_t* index, float* depth, float* bary, uint8_t* cover, const float* attr,
+                     const float* tex, const float* bg_host, const mer_shading* shading_host, float* image,
+                     int persistent_ctas, void* stream);
+/* cover: [pixels] uint8 or NULL, as for mer_backward (written by mer_batch_rasterize / mer_batch_render
+ * with the same index image). */
 int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,
-                       const mer_batch_totals* totals, const int32_t* index, const float* image,
+                       const mer_batch_totals* totals, const int32_t* index, const uint8_t* cover,
+                       const float* image,
                        const float* grad_image, const float* attr, const float* tex,
                        const mer_shading* shading_host, int terms, double* grad_vpix, float* grad_attr,
                        void* workspace, int persistent_ctas, void* stream);

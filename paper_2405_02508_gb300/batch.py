@@ -26,9 +26,10 @@ from .render import Renderer
 
 class BatchRenderer:
     def __init__(self, meshes, items, cams, shading, C_attr: int, tex=None, tile: int = 32, persistent_ctas: int = 0,
-                 device: str = "cuda"):
+                 device: str = "cuda", cover_hint: bool = True):
         """meshes: list of (verts [V,3] float32, tris [T,3] int32); items: list of (mesh, cam, H, W);
-        cams: structured camera array; tex: texture tensor on the device or None."""
+        cams: structured camera array; tex: texture tensor on the device or None.  cover_hint: the raster also
+        writes the cover image and the backward skips the pixel pairs it shows cannot scatter (same results)."""
         self.device = device
         self.shading = shading
         self.C = shading.C
@@ -61,6 +62,7 @@ class BatchRenderer:
         self.vpix = torch.empty((max(tot.vrecs, 1), B.VERTEX_FLOATS), dtype=torch.float32, device=device)
         self.index = torch.empty(max(tot.pixels, 1), dtype=torch.int32, device=device)
         self.image = torch.empty((max(tot.pixels, 1), self.C), dtype=torch.float32, device=device)
+        self.cover = torch.empty(max(tot.pixels, 1), dtype=torch.uint8, device=device) if cover_hint else None
         self.grad_vpix = torch.zeros((max(tot.vrecs, 1), 3), dtype=torch.float64, device=device)
         self.grad_verts = torch.zeros((max(self.n_verts, 1), 3), dtype=torch.float32, device=device)
         self._alloc_workspace(0)
@@ -77,10 +79,10 @@ class BatchRenderer:
         B.mer_batch_project(verts, self.cams, self.items, self.tot, self.vpix)
         if fused:
             B.mer_batch_render(self.vpix, self.tris, self.items, self.tot, self.workspace, self.index, attr, tex,
-                               self.bg, self.sh, self.image, depth, bary, self.persistent_ctas)
+                               self.bg, self.sh, self.image, depth, bary, self.persistent_ctas, self.cover)
             return self.image
         B.mer_batch_rasterize(self.vpix, self.tris, self.items, self.tot, self.workspace, self.index, depth, bary,
-                              self.persistent_ctas)
+                              self.persistent_ctas, self.cover)
         B.mer_batch_shade(self.vpix, self.tris, self.items, self.tot, self.index, attr, tex, self.bg, self.sh,
                           self.image, self.workspace)
         return self.image
@@ -89,7 +91,8 @@ class BatchRenderer:
         self.grad_vpix.zero_()
         self.grad_verts.zero_()
         B.mer_batch_backward(self.vpix, self.tris, self.items, self.tot, self.index, self.image, grad_image, attr, tex,
-                             self.sh, terms, self.grad_vpix, grad_attr, self.workspace, self.persistent_ctas)
+                             self.sh, terms, self.grad_vpix, grad_attr, self.workspace, self.persistent_ctas,
+                             self.cover)
         B.mer_batch_project_backward(self.cams, self.items, self.tot, self.vpix, self.grad_vpix, self.grad_verts)
         return self.grad_verts
 
@@ -155,12 +158,12 @@ class PlainRenderer:
     """Comparison path: each item rendered by its own multi-stage launch sequence."""
 
     def __init__(self, meshes, items, cams, shading, C_attr: int, tex_shape=None, tile: int = 32,
-                 device: str = "cuda"):
+                 device: str = "cuda", cover_hint: bool = True):
         self.meshes = meshes
         self.items = items
         self.cams = [B.cameras_tensor(cams[c:c + 1], device) for (_, c, _, _) in items]
         self.r = [Renderer(torch.from_numpy(np.asarray(meshes[m][1], np.int32)), len(meshes[m][0]), 1, H, W, shading,
-                           C_attr, tex_shape, tile, device) for (m, _, H, W) in items]
+                           C_attr, tex_shape, tile, device, cover_hint) for (m, _, H, W) in items]
 
     def step(self, verts_list, attr_list, grads, tex=None, checked=False):
         out = []

@@ -55,10 +55,10 @@ _SIGS = {
     "mer_workspace_size": ([_I, _I, _I, _I, _I, _I, _L], _Z),
     "mer_project": ([_P, _I, _P, _I, _P, _P], _I),
     "mer_project_screen": ([_P, _I, _I, _P, _P], _I),
-    "mer_rasterize": ([_P, _I, _P, _I, _I, _I, _I, _I, _P, _Z, _P, _P, _P, _P], _I),
+    "mer_rasterize": ([_P, _I, _P, _I, _I, _I, _I, _I, _P, _Z, _P, _P, _P, _P, _P], _I),
     "mer_shade": ([_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(MerShading), _P, _P, _P], _I),
-    "mer_backward": ([_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P, ctypes.POINTER(MerShading), _I, _P, _P, _P,
-                      _P], _I),
+    "mer_backward": ([_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, ctypes.POINTER(MerShading), _I, _P, _P,
+                      _P, _P], _I),
     "mer_edge_grad_backward": ([_P, _P, _I, _P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _P, _P], _I),
     "mer_interpolate_backward": ([_P, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "mer_project_backward": ([_I, _P, _I, _P, _P, _P, _P], _I),
@@ -79,12 +79,12 @@ _SIGS = {
     "mer_batch_plan": ([_P, _I, _I, ctypes.POINTER(MerBatchTotals)], _I),
     "mer_batch_workspace_size": ([ctypes.POINTER(MerBatchTotals), _L], _Z),
     "mer_batch_project": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _P], _I),
-    "mer_batch_rasterize": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _Z, _P, _P, _P, _I, _P], _I),
+    "mer_batch_rasterize": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _Z, _P, _P, _P, _P, _I, _P], _I),
     "mer_batch_shade": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P, ctypes.POINTER(MerShading), _P,
                          _P, _P], _I),
-    "mer_batch_render": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _Z, _P, _P, _P, _P, _P, _P,
+    "mer_batch_render": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _Z, _P, _P, _P, _P, _P, _P, _P,
                           ctypes.POINTER(MerShading), _P, _I, _P], _I),
-    "mer_batch_backward": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P, _P,
+    "mer_batch_backward": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P, _P, _P,
                             ctypes.POINTER(MerShading), _I, _P, _P, _P, _I, _P], _I),
     "mer_batch_project_backward": ([_P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P], _I),
 }
@@ -179,12 +179,12 @@ def mer_project_screen(scr: torch.Tensor, vpix: torch.Tensor):
     _check(lib().mer_project_screen(_ptr(scr), V, n, _ptr(vpix), _stream()), "mer_project_screen")
 
 
-def mer_rasterize(vpix, tris, H, W, tile, workspace, index, depth=None, bary=None):
+def mer_rasterize(vpix, tris, H, W, tile, workspace, index, depth=None, bary=None, cover=None):
     n, V = vpix.shape[0], vpix.shape[1]
     T = tris.shape[0]
     _check(lib().mer_rasterize(_ptr(vpix), V, _ptr(tris), T, n, H, W, tile, _ptr(workspace),
                                workspace.numel() * workspace.element_size(), _ptr(index), _ptr(depth), _ptr(bary),
-                               _stream()), "mer_rasterize")
+                               _ptr(cover), _stream()), "mer_rasterize")
 
 
 def mer_shade(vpix, tris, index, attr, tex, bg: np.ndarray, sh: MerShading, image, status_ws=None):
@@ -197,10 +197,10 @@ def mer_shade(vpix, tris, index, attr, tex, bg: np.ndarray, sh: MerShading, imag
 
 
 def mer_backward(vpix, tris, index, image, grad_image, attr, tex, sh: MerShading, terms: int, grad_vpix,
-                 grad_attr=None, status_ws=None):
+                 grad_attr=None, status_ws=None, cover=None):
     n, V = vpix.shape[0], vpix.shape[1]
     H, W = index.shape[1], index.shape[2]
-    _check(lib().mer_backward(_ptr(vpix), V, _ptr(tris), tris.shape[0], n, H, W, _ptr(index), _ptr(image),
+    _check(lib().mer_backward(_ptr(vpix), V, _ptr(tris), tris.shape[0], n, H, W, _ptr(index), _ptr(cover), _ptr(image),
                               _ptr(grad_image), _ptr(attr), _ptr(tex), ctypes.byref(sh), terms, _ptr(grad_vpix),
                               _ptr(grad_attr), _ptr(status_ws), _stream()), "mer_backward")
 
@@ -331,10 +331,11 @@ def mer_batch_project(verts, cams, items_dev, tot, vpix):
            "mer_batch_project")
 
 
-def mer_batch_rasterize(vpix, tris, items_dev, tot, workspace, index, depth=None, bary=None, persistent_ctas=0):
+def mer_batch_rasterize(vpix, tris, items_dev, tot, workspace, index, depth=None, bary=None, persistent_ctas=0,
+                        cover=None):
     _check(lib().mer_batch_rasterize(_ptr(vpix), _ptr(tris), _ptr(items_dev), ctypes.byref(tot), _ptr(workspace),
                                      workspace.numel() * workspace.element_size(), _ptr(index), _ptr(depth),
-                                     _ptr(bary), persistent_ctas, _stream()), "mer_batch_rasterize")
+                                     _ptr(bary), _ptr(cover), persistent_ctas, _stream()), "mer_batch_rasterize")
 
 
 def mer_batch_shade(vpix, tris, items_dev, tot, index, attr, tex, bg, sh: MerShading, image, status_ws=None):
@@ -345,18 +346,18 @@ def mer_batch_shade(vpix, tris, items_dev, tot, index, attr, tex, bg, sh: MerSha
 
 
 def mer_batch_render(vpix, tris, items_dev, tot, workspace, index, attr, tex, bg, sh: MerShading, image, depth=None,
-                     bary=None, persistent_ctas=0):
+                     bary=None, persistent_ctas=0, cover=None):
     bgc = (ctypes.c_float * max(1, sh.C))(*[float(x) for x in bg])
     _check(lib().mer_batch_render(_ptr(vpix), _ptr(tris), _ptr(items_dev), ctypes.byref(tot), _ptr(workspace),
                                   workspace.numel() * workspace.element_size(), _ptr(index), _ptr(depth), _ptr(bary),
-                                  _ptr(attr), _ptr(tex), ctypes.cast(bgc, ctypes.c_void_p), ctypes.byref(sh),
+                                  _ptr(cover), _ptr(attr), _ptr(tex), ctypes.cast(bgc, ctypes.c_void_p), ctypes.byref(sh),
                                   _ptr(image), persistent_ctas, _stream()), "mer_batch_render")
 
 
 def mer_batch_backward(vpix, tris, items_dev, tot, index, image, grad_image, attr, tex, sh: MerShading, terms: int,
-                       grad_vpix, grad_attr, workspace, persistent_ctas=0):
+                       grad_vpix, grad_attr, workspace, persistent_ctas=0, cover=None):
     _check(lib().mer_batch_backward(_ptr(vpix), _ptr(tris), _ptr(items_dev), ctypes.byref(tot), _ptr(index),
-                                    _ptr(image), _ptr(grad_image), _ptr(attr), _ptr(tex), ctypes.byref(sh), terms,
+                                    _ptr(cover), _ptr(image), _ptr(grad_image), _ptr(attr), _ptr(tex), ctypes.byref(sh), terms,
                                     _ptr(grad_vpix), _ptr(grad_attr), _ptr(workspace), persistent_ctas, _stream()),
            "mer_batch_backward")
 

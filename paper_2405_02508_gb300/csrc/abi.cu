@@ -12,19 +12,19 @@ extern "C" int mer_launch_project_backward(int, const mer_camera*, int, const me
                                            cudaStream_t);
 extern "C" size_t mer_raster_workspace_size(int, int, int, int, int, int, long long);
 extern "C" int mer_launch_rasterize(const mer_vertex*, int, const int*, int, int, int, int, int, void*, size_t, int*,
-                                    float*, float*, cudaStream_t);
+                                    float*, float*, unsigned char*, cudaStream_t);
 extern "C" int mer_launch_shade(const mer_vertex*, int, const int*, int, int, int, int, const int*, const float*,
                                 const float*, const float*, const mer_shading*, float*, void*, cudaStream_t);
-extern "C" int mer_launch_backward(const mer_vertex*, int, const int*, int, int, int, int, const int*, const float*,
-                                   const float*, const float*, const float*, const mer_shading*, int, double*, float*,
-                                   void*, cudaStream_t);
+extern "C" int mer_launch_backward(const mer_vertex*, int, const int*, int, int, int, int, const int*,
+                                   const unsigned char*, const float*, const float*, const float*, const float*,
+                                   const mer_shading*, int, double*, float*, void*, cudaStream_t);
 
 extern "C" size_t mer_batch_raster_workspace_size(long long, long long, long long);
 extern "C" int mer_launch_batch_rasterize(const mer_vertex*, const int*, const mer_item*, int, long long, long long, int,
-                                          void*, size_t, int*, float*, float*, int, cudaStream_t);
+                                          void*, size_t, int*, float*, float*, unsigned char*, int, cudaStream_t);
 extern "C" int mer_launch_batch_render(const mer_vertex*, const int*, const mer_item*, int, long long, long long, int,
-                                       void*, size_t, int*, float*, float*, const float*, const float*, const float*,
-                                       const mer_shading*, float*, int, cudaStream_t);
+                                       void*, size_t, int*, float*, float*, unsigned char*, const float*, const float*,
+                                       const float*, const mer_shading*, float*, int, cudaStream_t);
 extern "C" int mer_launch_forward_grad(const mer_vertex*, int, const int*, int, int, int, int, const int*, const float*,
                                        const float*, const float*, const float*, const mer_shading*, int, float*, void*,
                                        cudaStream_t);
@@ -37,8 +37,9 @@ extern "C" int mer_launch_shade_batch(const mer_vertex*, const int*, const mer_i
                                       const float*, const float*, const float*, const mer_shading*, float*, void*,
                                       cudaStream_t);
 extern "C" int mer_launch_backward_batch(const mer_vertex*, const int*, const mer_item*, int, long long, const int*,
-                                         const float*, const float*, const float*, const float*, const mer_shading*,
-                                         int, double*, float*, void*, int, cudaStream_t);
+                                         const unsigned char*, const float*, const float*, const float*,
+                                         const float*, const mer_shading*, int, double*, float*, void*, int,
+                                         cudaStream_t);
 
 namespace {
 
@@ -108,7 +109,8 @@ int mer_rasterize_world(const float* verts, int V, const int32_t* tris, int T, c
     if (V > 0 && (!verts || !cams || !vpix)) return MER_EINVAL;
     const int rc = mer_project(verts, V, cams, n, vpix, stream);
     if (rc != MER_OK) return rc;
-    return mer_rasterize(vpix, V, tris, T, n, H, W, tile, workspace, workspace_bytes, index, depth, bary, stream);
+    return mer_rasterize(vpix, V, tris, T, n, H, W, tile, workspace, workspace_bytes, index, depth, bary, nullptr,
+                         stream);
 }
 
 int mer_project_screen(const double* scr, int V, int n, mer_vertex* vpix, void* stream) {
@@ -119,7 +121,8 @@ int mer_project_screen(const double* scr, int V, int n, mer_vertex* vpix, void* 
 }
 
 int mer_rasterize(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W, int tile,
-                  void* workspace, size_t workspace_bytes, int32_t* index, float* depth, float* bary, void* stream) {
+                  void* workspace, size_t workspace_bytes, int32_t* index, float* depth, float* bary, uint8_t* cover,
+                  void* stream) {
     if (V < 0 || T < 0 || !dims_ok(n, H, W)) return MER_EINVAL;
     if (tile != 8 && tile != 16 && tile != 32) return MER_EINVAL;
     if ((long long)n * H * W == 0) return MER_OK;
@@ -127,7 +130,7 @@ int mer_rasterize(const mer_vertex* vpix, int V, const int32_t* tris, int T, int
     if (T > 0 && (!tris || !vpix)) return MER_EINVAL;
     if (workspace_bytes < mer_raster_workspace_size(V, T, n, H, W, tile, 1)) return MER_EINVAL;
     return mer_launch_rasterize(vpix, V, tris, T, n, H, W, tile, workspace, workspace_bytes, index, depth, bary,
-                                S(stream));
+                                cover, S(stream));
 }
 
 int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W, const int32_t* index,
@@ -144,7 +147,7 @@ int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, 
 }
 
 int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W, const int32_t* index,
-                 const float* image, const float* grad_image, const float* attr, const float* tex,
+                 const uint8_t* cover, const float* image, const float* grad_image, const float* attr, const float* tex,
                  const mer_shading* sh, int terms, double* grad_vpix, float* grad_attr, void* status_ws, void* stream) {
     if (V < 0 || T < 0 || !dims_ok(n, H, W) || !shading_ok(sh)) return MER_EINVAL;
     if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT | MER_EXACT_CROSSING)) return MER_EINVAL;
@@ -156,7 +159,7 @@ int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int 
     if ((terms & MER_INTERIOR) && sh->uv_offset >= 0 && !tex) return MER_EINVAL;
     if (grad_attr && sh->uv_offset < 0 && sh->n_main > 4) return MER_EINVAL;  // attribute gradients: <= 4 channels
     if (status_ws && !aligned256(status_ws)) return MER_EINVAL;
-    return mer_launch_backward(vpix, V, tris, T, n, H, W, index, image, grad_image, attr, tex, sh, terms, grad_vpix,
+    return mer_launch_backward(vpix, V, tris, T, n, H, W, index, cover, image, grad_image, attr, tex, sh, terms, grad_vpix,
                                grad_attr, status_ws, S(stream));
 }
 
@@ -188,7 +191,7 @@ int mer_edge_grad_backward(const float* image, const float* grad_image, int C, c
                            const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
                            int intersections, double* grad_vpix, void* status_ws, void* stream) {
     mer_shading sh = {0, C, -1, -1, -1, 0, 0, 0, 0, -1};
-    return mer_backward(vpix, V, tris, T, n, H, W, index, image, grad_image, nullptr, nullptr, &sh,
+    return mer_backward(vpix, V, tris, T, n, H, W, index, nullptr, image, grad_image, nullptr, nullptr, &sh,
                         MER_EDGE | (intersections ? MER_INTERSECT : 0), grad_vpix, nullptr, status_ws, stream);
 }
 
@@ -196,7 +199,7 @@ int mer_interpolate_backward(const float* attr, int C_attr, const int32_t* tris,
                              const int32_t* index, int n, int H, int W, const float* grad_out, float* grad_attr,
                              double* grad_vpix, void* status_ws, void* stream) {
     mer_shading sh = {C_attr, C_attr, -1, -1, -1, C_attr, 0, 0, 0, -1};
-    return mer_backward(vpix, V, tris, T, n, H, W, index, nullptr, grad_out, attr, nullptr, &sh, MER_INTERIOR,
+    return mer_backward(vpix, V, tris, T, n, H, W, index, nullptr, nullptr, grad_out, attr, nullptr, &sh, MER_INTERIOR,
                         grad_vpix, grad_attr, status_ws, stream);
 }
 
@@ -261,14 +264,14 @@ int mer_batch_project(const float* verts, const mer_camera* cams, const mer_item
 
 int mer_batch_rasterize(const mer_vertex* vpix, const int32_t* tris, const mer_item* items, const mer_batch_totals* t,
                         void* workspace, size_t workspace_bytes, int32_t* index, float* depth, float* bary,
-                        int persistent_ctas, void* stream) {
+                        uint8_t* cover, int persistent_ctas, void* stream) {
     if (!totals_ok(t, items) || (t->tile != 16 && t->tile != 32 && t->tile != 64)) return MER_EINVAL;
     if (t->pixels == 0) return MER_OK;
     if (!workspace || !aligned256(workspace) || !index || persistent_ctas < 0) return MER_EINVAL;
     if (t->trecs > 0 && (!tris || !vpix)) return MER_EINVAL;
     if (workspace_bytes < mer_batch_raster_workspace_size(t->tiles, t->trecs, 1)) return MER_EINVAL;
     return mer_launch_batch_rasterize(vpix, tris, items, t->n_items, t->trecs, t->tiles, t->tile, workspace,
-                                      workspace_bytes, index, depth, bary, persistent_ctas, S(stream));
+                                      workspace_bytes, index, depth, bary, cover, persistent_ctas, S(stream));
 }
 
 int mer_batch_shade(const mer_vertex* vpix, const int32_t* tris, const mer_item* items, const mer_batch_totals* t,
@@ -286,8 +289,8 @@ int mer_batch_shade(const mer_vertex* vpix, const int32_t* tris, const mer_item*
 
 int mer_batch_render(const mer_vertex* vpix, const int32_t* tris, const mer_item* items, const mer_batch_totals* t,
                      void* workspace, size_t workspace_bytes, int32_t* index, float* depth, float* bary,
-                     const float* attr, const float* tex, const float* bg_host, const mer_shading* sh, float* image,
-                     int persistent_ctas, void* stream) {
+                     uint8_t* cover, const float* attr, const float* tex, const float* bg_host, const mer_shading* sh,
+                     float* image, int persistent_ctas, void* stream) {
     if (!totals_ok(t, items) || (t->tile != 16 && t->tile != 32 && t->tile != 64) || !shading_ok(sh)) return MER_EINVAL;
     if (t->pixels == 0) return MER_OK;
     if (!workspace || !aligned256(workspace) || !index || !image || persistent_ctas < 0) return MER_EINVAL;
@@ -296,14 +299,14 @@ int mer_batch_render(const mer_vertex* vpix, const int32_t* tris, const mer_item
     if (sh->uv_offset >= 0 && !tex) return MER_EINVAL;
     if (workspace_bytes < mer_batch_raster_workspace_size(t->tiles, t->trecs, 1)) return MER_EINVAL;
     return mer_launch_batch_render(vpix, tris, items, t->n_items, t->trecs, t->tiles, t->tile, workspace,
-                                   workspace_bytes, index, depth, bary, attr, tex, bg_host, sh, image, persistent_ctas,
+                                   workspace_bytes, index, depth, bary, cover, attr, tex, bg_host, sh, image, persistent_ctas,
                                    S(stream));
 }
 
 int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_item* items, const mer_batch_totals* t,
-                       const int32_t* index, const float* image, const float* grad_image, const float* attr,
-                       const float* tex, const mer_shading* sh, int terms, double* grad_vpix, float* grad_attr,
-                       void* workspace, int persistent_ctas, void* stream) {
+                       const int32_t* index, const uint8_t* cover, const float* image, const float* grad_image,
+                       const float* attr, const float* tex, const mer_shading* sh, int terms, double* grad_vpix,
+                       float* grad_attr, void* workspace, int persistent_ctas, void* stream) {
     if (!totals_ok(t, items) || !shading_ok(sh)) return MER_EINVAL;
     if (terms & ~(MER_EDGE | MER_INTERIOR | MER_INTERSECT | MER_EXACT_CROSSING)) return MER_EINVAL;
     if (t->pixels == 0 || terms == 0) return MER_OK;
@@ -313,8 +316,8 @@ int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_it
     if ((terms & MER_INTERIOR) && sh->uv_offset >= 0 && !tex) return MER_EINVAL;
     if (grad_attr && sh->uv_offset < 0 && sh->n_main > 4) return MER_EINVAL;  // attribute gradients: <= 4 channels
     if (!workspace || !aligned256(workspace) || persistent_ctas < 0) return MER_EINVAL;
-    return mer_launch_backward_batch(vpix, tris, items, t->n_items, t->btiles, index, image, grad_image, attr, tex, sh,
-                                     terms, grad_vpix, grad_attr, workspace, persistent_ctas, S(stream));
+    return mer_launch_backward_batch(vpix, tris, items, t->n_items, t->btiles, index, cover, image, grad_image, attr,
+                                     tex, sh, terms, grad_vpix, grad_attr, workspace, persistent_ctas, S(stream));
 }
 
 int mer_batch_project_backward(const mer_camera* cams, const mer_item* items, const mer_batch_totals* t,

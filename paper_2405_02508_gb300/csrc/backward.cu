@@ -88,6 +88,7 @@ struct BItem {
     const mer_vertex* vb;   // vertex records
     const int* tris;        // triangles (item-local vertex ids)
     const int* index;       // index image [H, W]
+    const unsigned char* cover;  // cover image [H, W] (MER_COVER_* bits) or null
     const float* image;     // shaded image [H, W, C]
     const float* grad;      // dL/d image [H, W, C]
     const float* attr;      // attributes [V, C_attr]
@@ -101,6 +102,7 @@ constexpr int kMaxA = 4;  // most attribute-gradient channels carried through th
 template <int NA, bool EXACT>
 struct BwdShared {
     int sidx[kHH][kHW];
+    unsigned char scov[kHH][kHW];  // cover image of the tile and halo (when given)
     int skey[kSlots];
     float sval[kSlots][3];
     float sattr[NA > 0 ? kSlots : 1][NA > 0 ? NA : 1];
@@ -123,16 +125,31 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
     unsigned m[kM];  // per (row k, direction d): lanes whose pixel is covered and whose neighbour in d differs
     int np[kM + 1];  // prefix counts
     np[0] = 0;
+    const bool hinted = it.cover != nullptr;
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
         const int row = r0 + k;
         const int t = S.sidx[row + 1][lane + 1];  // -2 outside the image
+        const unsigned hp = hinted ? S.scov[row + 1][lane + 1] : 0u;
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
             const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
             const int ddy = d == 2 ? -1 : (d == 3 ? 1 : 0);
             const int tq = S.sidx[row + 1 + ddy][lane + 1 + ddx];
-            m[4 * k + d] = __ballot_sync(full, t >= 0 && tq != t && tq != -2);
+            bool pair = t >= 0 && tq != t && tq != -2;
+            if (hinted && tq >= 0) {
+                // p's fragment can scatter only if q's triangle covers p's centre too (Sec. 4.3), which needs
+                // another triangle of q's facing at p (a second one when p's own triangle has that facing);
+                // a pair across the border of p's bin tile is always classified
+                const unsigned hq = S.scov[row + 1 + ddy][lane + 1 + ddx];
+                const bool same = ((hp ^ hq) & MER_COVER_WINNER_BACK) == 0;
+                const unsigned need = same ? MER_COVER_SAME_2 : MER_COVER_OTHER_1;
+                const unsigned border = d == 0 ? MER_COVER_BORDER_L
+                                                : (d == 1 ? MER_COVER_BORDER_R
+                                                          : (d == 2 ? MER_COVER_BORDER_T : MER_COVER_BORDER_B));
+                pair = pair && (hp & (need | border)) != 0;
+            }
+            m[4 * k + d] = __ballot_sync(full, pair);
             np[4 * k + d + 1] = np[4 * k + d] + __popc(m[4 * k + d]);
         }
     }
@@ -309,8 +326,10 @@ __device__ __forceinline__ bool tile_halo(const BItem& it, int tx, int ty, BwdSh
     for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
         const int hy = i / kHW, hx = i % kHW;
         const int gx = tx * kTW + hx - 1, gy = ty * kTH + hy - 1;
-        const int v = (gx >= 0 && gx < it.W && gy >= 0 && gy < it.H) ? __ldg(it.index + (size_t)gy * it.W + gx) : -2;
+        const bool in = gx >= 0 && gx < it.W && gy >= 0 && gy < it.H;
+        const int v = in ? __ldg(it.index + (size_t)gy * it.W + gx) : -2;
         S.sidx[hy][hx] = v;
+        if (it.cover) S.scov[hy][hx] = in ? __ldg(it.cover + (size_t)gy * it.W + gx) : (unsigned char)0;
         covered |= v >= 0 && hy >= 1 && hy <= kTH && hx >= 1 && hx <= kTW;
     }
     return covered;
@@ -570,7 +589,9 @@ __device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, Bw
 
 template <int NA, bool EXACT>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
-                                                       const int* __restrict__ index, const float* __restrict__ image,
+                                                       const int* __restrict__ index,
+                                                       const unsigned char* __restrict__ cover,
+                                                       const float* __restrict__ image,
                                                        const float* __restrict__ grad, const float* __restrict__ attr,
                                                        const float* __restrict__ tex, BwdArgs a,
                                                        double* __restrict__ grad_vpix, float* __restrict__ grad_attr,
@@ -584,6 +605,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward(const mer_ver
     it.vb = vpix + (size_t)view * a.V;
     it.tris = tris;
     it.index = index + (size_t)view * plane;
+    it.cover = cover ? cover + (size_t)view * plane : nullptr;
     it.image = image ? image + (size_t)view * plane * a.sh.C : nullptr;
     it.grad = grad + (size_t)view * plane * a.sh.C;
     it.attr = attr;
@@ -604,6 +626,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward_batch(const m
                                                              const int* __restrict__ tris,
                                                              const mer_item* __restrict__ items, int n_items,
                                                              long long btiles, const int* __restrict__ index,
+                                                             const unsigned char* __restrict__ cover,
                                                              const float* __restrict__ image,
                                                              const float* __restrict__ grad,
                                                              const float* __restrict__ attr,
@@ -640,6 +663,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward_batch(const m
         it.vb = vpix + m.vrec;
         it.tris = tris + 3 * m.tri;
         it.index = index + m.pix;
+        it.cover = cover ? cover + m.pix : nullptr;
         it.image = image ? image + (size_t)m.pix * C : nullptr;
         it.grad = grad + (size_t)m.pix * C;
         it.attr = attr ? attr + (size_t)m.vert * Ca : nullptr;
@@ -671,8 +695,8 @@ int attr_channels(const mer_shading* sh, const float* grad_attr) {
 }  // namespace
 
 extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
-                                         long long btiles, const int* index, const float* image,
-                                         const float* grad_image, const float* attr, const float* tex,
+                                         long long btiles, const int* index, const unsigned char* cover,
+                                         const float* image, const float* grad_image, const float* attr, const float* tex,
                                          const mer_shading* sh, int terms, double* grad_vpix, float* grad_attr,
                                          void* ws, int persistent_ctas, cudaStream_t s) {
     if (btiles == 0) return 0;
@@ -697,7 +721,7 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
     }
     const bool exact = (terms & MER_EXACT_CROSSING) != 0;
 #define MER_BWD_BATCH(A, E)                                                                                        \
-    k_backward_batch<A, E><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, image, grad_image, \
+    k_backward_batch<A, E><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, cover, image, grad_image, \
                                                      attr, tex, a, grad_vpix, grad_attr, ws)
     switch (attr_channels(sh, grad_attr) * 2 + (exact ? 1 : 0)) {
         case 0: MER_BWD_BATCH(0, false); break;
@@ -717,7 +741,7 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
 }
 
 extern "C" int mer_launch_backward(const mer_vertex* vpix, int V, const int* tris, int T, int n, int H, int W,
-                                   const int* index, const float* image, const float* grad_image, const float* attr,
+                                   const int* index, const unsigned char* cover, const float* image, const float* grad_image, const float* attr,
                                    const float* tex, const mer_shading* sh, int terms, double* grad_vpix,
                                    float* grad_attr, void* ws, cudaStream_t s) {
     BwdArgs a;
@@ -732,7 +756,7 @@ extern "C" int mer_launch_backward(const mer_vertex* vpix, int V, const int* tri
     if (blocks == 0) return 0;
     const bool exact = (terms & MER_EXACT_CROSSING) != 0;
 #define MER_BWD(A, E)                                                                                             \
-    k_backward<A, E><<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, image, grad_image, attr, tex, a,     \
+    k_backward<A, E><<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, cover, image, grad_image, attr, tex, a, \
                                                            grad_vpix, grad_attr, ws)
     switch (attr_channels(sh, grad_attr) * 2 + (exact ? 1 : 0)) {
         case 0: MER_BWD(0, false); break;

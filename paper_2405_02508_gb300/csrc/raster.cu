@@ -224,25 +224,34 @@ __global__ void k_scan_add(int* __restrict__ out, long long N, const int* __rest
 constexpr int kStage = 256;  // triangle records staged per round
 constexpr int kRasterThreads = 256;
 
+// Per-pixel bits kept in shared memory for the cover image: a front-facing triangle covered the centre
+// (taken when the front part is done), two or more did, one / two or more back-facing ones did, and a
+// back-facing fragment raised the depth buffer (the winner is then back-facing: the front part is drawn
+// first, so every later raise comes from a back-facing fragment).
+constexpr unsigned kCovF1 = 1, kCovF2 = 2, kCovB1 = 4, kCovB2 = 8, kCovWB = 16;
+
 template <int TS>
 struct RasterShared {
     static constexpr int kStageTS = TS >= 64 ? 160 : kStage;  // keeps the 64 x 64 tile within 48 KB
     TriRaster rec[kStageTS];
     int id[kStageTS];
     unsigned long long zbuf[TS * TS];
+    unsigned cov[TS * TS / 4];  // cover-image bits (kCov*), one byte a pixel
     float red[kRasterThreads / 32];
 };
 
 // Smallest depth key (zeta_test) over the tile's pixels inside the image, 0 if one of them is still empty.
 // All threads call it; it starts and ends with a barrier.
+// With `cover`, also records which pixels a front-facing triangle covers (kCovF1).
 template <int TS>
-__device__ __forceinline__ float tile_min_zeta(RasterShared<TS>& S, int ox, int oy, int W, int H) {
+__device__ __forceinline__ float tile_min_zeta(RasterShared<TS>& S, int ox, int oy, int W, int H, bool cover) {
     __syncthreads();
     float mn = 3.0e38f;
     for (int i = threadIdx.x; i < TS * TS; i += kRasterThreads) {
         const int px = ox + (i % TS), py = oy + (i / TS);
         if (px >= W || py >= H) continue;
         const unsigned long long key = S.zbuf[i];
+        if (cover && key) atomicOr(&S.cov[i >> 2], kCovF1 << ((i & 3) * 8));
         mn = fminf(mn, key ? __uint_as_float((unsigned)(key >> 32)) : 0.0f);
     }
 #pragma unroll
@@ -258,6 +267,11 @@ __device__ __forceinline__ float tile_min_zeta(RasterShared<TS>& S, int ox, int 
 
 // SHADE: also shade every pixel of the tile from its z-buffer winner (shade_fragment, as the deferred
 // shading kernels do from the index image).
+// cover (optional): one byte a pixel (MER_COVER_* bits): whether another triangle of the winner's facing,
+// or one of the other facing, covers the pixel centre, the facing of the winner and which borders of its bin
+// tile the pixel lies on, from the kCov* bits.  The counts leave out the triangles of the second part that
+// are skipped as hidden, which win no pixel of this tile, so they are exact for every triangle that wins a
+// pixel of the same bin tile.
 // The tile's list holds the camera-facing triangles first (nfront of them) and the others after; before
 // the second part the tile's smallest depth key is taken, and a triangle of that part whose largest vertex
 // zeta (with a margin above the FP32 rounding of the key) is below it cannot win any pixel: it is skipped.
@@ -266,12 +280,15 @@ __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, con
                                             const int* __restrict__ cnts, const int* __restrict__ nfront,
                                             const int* __restrict__ list, bool overflow, RasterShared<TS>& S,
                                             int* __restrict__ index, float* __restrict__ depth,
-                                            float* __restrict__ bary, const ShadeOut& so, void* ws) {
+                                            float* __restrict__ bary, unsigned char* __restrict__ cover,
+                                            const ShadeOut& so, void* ws) {
     constexpr int kSt = RasterShared<TS>::kStageTS;
     const long long tile = it.tile0 + local_tile;
     const int ty = local_tile / it.ntx, tx = local_tile % it.ntx;
     const int ox = tx * TS, oy = ty * TS;
     for (int i = threadIdx.x; i < TS * TS; i += kRasterThreads) S.zbuf[i] = 0ull;
+    if (cover)
+        for (int i = threadIdx.x; i < TS * TS / 4; i += kRasterThreads) S.cov[i] = 0u;
     const int count = overflow ? 0 : cnts[tile];
     const int off = overflow ? 0 : offs[tile];
     const int nf = overflow ? 0 : min(nfront[tile], count);
@@ -283,7 +300,7 @@ __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, con
         // stage boundaries fall on the front / back split so each stage is one part
         const int lim = base < nf ? nf : count;
         m = min(kSt, lim - base);
-        if (base == nf && base > 0) zcull = tile_min_zeta<TS>(S, ox, oy, it.W, it.H);
+        if (base == nf && base > 0) zcull = tile_min_zeta<TS>(S, ox, oy, it.W, it.H, cover != nullptr);
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += kRasterThreads) {
             const int t = list[off + base + j];
@@ -324,7 +341,19 @@ __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, con
                     z = depth_key(r, E);
                 }
                 const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | idkey;
-                atomicMax(&S.zbuf[(py - oy) * TS + (px - ox)], key);
+                const int pi = (py - oy) * TS + (px - ox);
+                // the 64-bit maximum runs as a compare-and-swap loop: its old value costs nothing extra
+                const unsigned long long old = atomicMax(&S.zbuf[pi], key);
+                if (cover) {
+                    const unsigned sh = (pi & 3) * 8;
+                    if (!back) {
+                        if (old) atomicOr(&S.cov[pi >> 2], kCovF2 << sh);  // a front fragment came first
+                    } else {
+                        if (key > old) atomicOr(&S.cov[pi >> 2], kCovWB << sh);
+                        const unsigned o = atomicOr(&S.cov[pi >> 2], kCovB1 << sh);
+                        if (o & (kCovB1 << sh)) atomicOr(&S.cov[pi >> 2], kCovB2 << sh);
+                    }
+                }
             }
         }
     }
@@ -336,6 +365,21 @@ __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, con
         const int t = key ? (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull)) : -1;
         const size_t p = (size_t)it.pix0 + (size_t)py * it.W + px;
         index[p] = t;
+        if (cover) {
+            const int lx = i % TS, ly = i / TS;
+            unsigned c = (lx == 0 ? MER_COVER_BORDER_L : 0u) | (lx == TS - 1 ? MER_COVER_BORDER_R : 0u) |
+                         (ly == 0 ? MER_COVER_BORDER_T : 0u) | (ly == TS - 1 ? MER_COVER_BORDER_B : 0u);
+            if (t >= 0) {
+                const unsigned b = S.cov[i >> 2] >> ((i & 3) * 8);
+                if (b & kCovWB) {  // kCovF1 was taken before the back part (none if the tile has no front part)
+                    c |= MER_COVER_WINNER_BACK | ((b & kCovB2) ? MER_COVER_SAME_2 : 0u) |
+                         ((b & kCovF1) ? MER_COVER_OTHER_1 : 0u);
+                } else {
+                    c |= ((b & kCovF2) ? MER_COVER_SAME_2 : 0u) | ((b & kCovB1) ? MER_COVER_OTHER_1 : 0u);
+                }
+            }
+            cover[p] = (unsigned char)c;
+        }
         if (SHADE)
             shade_fragment(it.vpix, it.V, it.tris, it.T, t, px, py,
                            so.attr ? so.attr + (size_t)it.vert * so.a.sh.C_attr : nullptr, so.tex, so.a,
@@ -407,7 +451,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(TriRaster* __restrict
                                                            const int* __restrict__ list, const mer_vertex* __restrict__ vpix,
                                                            const int* __restrict__ tris, void* ws, long long capacity,
                                                            int* __restrict__ index, float* __restrict__ depth,
-                                                           float* __restrict__ bary) {
+                                                           float* __restrict__ bary, unsigned char* __restrict__ cover) {
     __shared__ RasterShared<TS> S;
     const WsHeader* hdr = reinterpret_cast<const WsHeader*>(ws);
     const bool overflow = hdr->total_bins > capacity;
@@ -417,7 +461,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster(TriRaster* __restrict
     ShadeOut none;
     none.attr = nullptr; none.tex = nullptr; none.image = nullptr;
     raster_tile<TS, false>(view_item(g, vpix, tris, recs, view), local, offs, cnts, nfront, list, overflow, S, index,
-                           depth, bary, none, ws);
+                           depth, bary, cover, none, ws);
 }
 
 // ---- batched entry: items from a table ----
@@ -474,7 +518,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_batch(TriRaster* __re
                                                                  const int* __restrict__ tris, void* ws,
                                                                  long long capacity, int* __restrict__ index,
                                                                  float* __restrict__ depth, float* __restrict__ bary,
-                                                                 ShadeOut so) {
+                                                                 unsigned char* __restrict__ cover, ShadeOut so) {
     __shared__ RasterShared<TS> S;
     __shared__ long long s_tile;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
@@ -495,7 +539,7 @@ __global__ void __launch_bounds__(kRasterThreads) k_raster_batch(TriRaster* __re
         }
         const mer_item m = b.items[cur];
         raster_tile<TS, SHADE>(batch_item(m, b.tile, vpix, tris, recs), (int)(g - m.tile), offs, cnts, nfront, list,
-                               overflow, S, index, depth, bary, so, ws);  // ends with a barrier: s_tile may be overwritten after it
+                               overflow, S, index, depth, bary, cover, so, ws);  // ends with a barrier: s_tile may be overwritten after it
     }
 }
 
@@ -555,7 +599,7 @@ extern "C" size_t mer_raster_workspace_size(int V, int T, int n, int H, int W, i
 
 extern "C" int mer_launch_rasterize(const mer_vertex* vpix, int V, const int* tris, int T, int n, int H, int W,
                                     int tile, void* ws, size_t ws_bytes, int* index, float* depth, float* bary,
-                                    cudaStream_t s) {
+                                    unsigned char* cover, cudaStream_t s) {
     // capacity: whatever the workspace holds beyond the fixed part
     RasterLayout L = raster_layout(V, T, n, H, W, tile, 1);
     if (ws_bytes < L.total) return 1;
@@ -583,9 +627,9 @@ extern "C" int mer_launch_rasterize(const mer_vertex* vpix, int V, const int* tr
                                                                 capacity);
     const unsigned grid = (unsigned)L.ntiles;
     switch (tile) {
-        case 8: k_raster<8><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, cursor, list, vpix, tris, hdr, capacity, index, depth, bary); break;
-        case 16: k_raster<16><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, cursor, list, vpix, tris, hdr, capacity, index, depth, bary); break;
-        case 32: k_raster<32><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, cursor, list, vpix, tris, hdr, capacity, index, depth, bary); break;
+        case 8: k_raster<8><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, cursor, list, vpix, tris, hdr, capacity, index, depth, bary, cover); break;
+        case 16: k_raster<16><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, cursor, list, vpix, tris, hdr, capacity, index, depth, bary, cover); break;
+        case 32: k_raster<32><<<grid, kRasterThreads, 0, s>>>(recs, g, offs, counts, cursor, list, vpix, tris, hdr, capacity, index, depth, bary, cover); break;
         default: return 1;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
@@ -598,7 +642,8 @@ extern "C" size_t mer_batch_raster_workspace_size(long long tiles, long long tre
 template <int TS, bool SHADE>
 static int launch_raster_batch(unsigned grid, TriRaster* recs, BatchGeom b, const int* offs, const int* counts,
                                const int* nfront, const int* list, const mer_vertex* vpix, const int* tris, void* hdr, long long capacity,
-                               int* index, float* depth, float* bary, const ShadeOut& so, cudaStream_t s) {
+                               int* index, float* depth, float* bary, unsigned char* cover, const ShadeOut& so,
+                               cudaStream_t s) {
     if (grid == 0) {
         int per_sm = 0, sms = 0, dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 2;
@@ -609,7 +654,7 @@ static int launch_raster_batch(unsigned grid, TriRaster* recs, BatchGeom b, cons
         grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
     }
     k_raster_batch<TS, SHADE><<<grid, kRasterThreads, 0, s>>>(recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity,
-                                                              index, depth, bary, so);
+                                                              index, depth, bary, cover, so);
     return 0;
 }
 
@@ -617,11 +662,11 @@ template <bool SHADE>
 static int launch_raster_batch_tile(int tile, unsigned grid, TriRaster* recs, BatchGeom b, const int* offs,
                                     const int* counts, const int* nfront, const int* list, const mer_vertex* vpix, const int* tris,
                                     void* hdr, long long capacity, int* index, float* depth, float* bary,
-                                    const ShadeOut& so, cudaStream_t s) {
+                                    unsigned char* cover, const ShadeOut& so, cudaStream_t s) {
     switch (tile) {
-        case 16: return launch_raster_batch<16, SHADE>(grid, recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
-        case 32: return launch_raster_batch<32, SHADE>(grid, recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
-        case 64: return launch_raster_batch<64, SHADE>(grid, recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity, index, depth, bary, so, s);
+        case 16: return launch_raster_batch<16, SHADE>(grid, recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity, index, depth, bary, cover, so, s);
+        case 32: return launch_raster_batch<32, SHADE>(grid, recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity, index, depth, bary, cover, so, s);
+        case 64: return launch_raster_batch<64, SHADE>(grid, recs, b, offs, counts, nfront, list, vpix, tris, hdr, capacity, index, depth, bary, cover, so, s);
         default: return 1;
     }
 }
@@ -629,7 +674,7 @@ static int launch_raster_batch_tile(int tile, unsigned grid, TriRaster* recs, Ba
 // Binning and the persistent raster of all items; with `so`, each resolved tile is shaded in the same pass.
 static int batch_raster(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items, long long trecs,
                         long long tiles, int tile, void* ws, size_t ws_bytes, int* index, float* depth, float* bary,
-                        const ShadeOut* so, int persistent_ctas, cudaStream_t s) {
+                        unsigned char* cover, const ShadeOut* so, int persistent_ctas, cudaStream_t s) {
     RasterLayout L = layout_for(tiles, trecs, 1);
     if (ws_bytes < L.total) return 1;
     const long long capacity = (long long)((ws_bytes - L.list) / 4);
@@ -654,9 +699,9 @@ static int batch_raster(const mer_vertex* vpix, const int* tris, const mer_item*
         ShadeOut none;
         none.attr = nullptr; none.tex = nullptr; none.image = nullptr;
         const int rc = so ? launch_raster_batch_tile<true>(tile, grid, recs, b, offs, counts, cursor, list, vpix, tris, hdr,
-                                                           capacity, index, depth, bary, *so, s)
+                                                           capacity, index, depth, bary, cover, *so, s)
                           : launch_raster_batch_tile<false>(tile, grid, recs, b, offs, counts, cursor, list, vpix, tris, hdr,
-                                                            capacity, index, depth, bary, none, s);
+                                                            capacity, index, depth, bary, cover, none, s);
         if (rc) return rc;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
@@ -664,23 +709,23 @@ static int batch_raster(const mer_vertex* vpix, const int* tris, const mer_item*
 
 extern "C" int mer_launch_batch_rasterize(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
                                           long long trecs, long long tiles, int tile, void* ws, size_t ws_bytes,
-                                          int* index, float* depth, float* bary, int persistent_ctas,
-                                          cudaStream_t s) {
-    return batch_raster(vpix, tris, items, n_items, trecs, tiles, tile, ws, ws_bytes, index, depth, bary, nullptr,
+                                          int* index, float* depth, float* bary, unsigned char* cover,
+                                          int persistent_ctas, cudaStream_t s) {
+    return batch_raster(vpix, tris, items, n_items, trecs, tiles, tile, ws, ws_bytes, index, depth, bary, cover, nullptr,
                         persistent_ctas, s);
 }
 
 extern "C" int mer_launch_batch_render(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
                                        long long trecs, long long tiles, int tile, void* ws, size_t ws_bytes,
-                                       int* index, float* depth, float* bary, const float* attr, const float* tex,
-                                       const float* bg, const mer_shading* sh, float* image, int persistent_ctas,
-                                       cudaStream_t s) {
+                                       int* index, float* depth, float* bary, unsigned char* cover, const float* attr,
+                                       const float* tex, const float* bg, const mer_shading* sh, float* image,
+                                       int persistent_ctas, cudaStream_t s) {
     ShadeOut so;
     so.a = make_shade_args(tex, bg, sh);
     so.attr = attr;
     so.tex = tex;
     so.image = image;
-    return batch_raster(vpix, tris, items, n_items, trecs, tiles, tile, ws, ws_bytes, index, depth, bary, &so,
+    return batch_raster(vpix, tris, items, n_items, trecs, tiles, tile, ws, ws_bytes, index, depth, bary, cover, &so,
                         persistent_ctas, s);
 }
 
@@ -733,7 +778,7 @@ extern "C" int mer_rasterize_noalloc(const mer_vertex* vpix, int V, const int32_
     // every call shares the array: clear the status word left by the previous call
     if (cudaMemsetAsync(ptr, 0, sizeof(WsHeader), s) != cudaSuccess) return MER_ECUDA;
     const int rc = mer_launch_rasterize(vpix, V, tris, T, n, H, W, tile, ptr, kNoAllocScratchBytes, index, depth,
-                                        bary, s);
+                                        bary, nullptr, s);
     if (rc != 0) return rc;
     if (status) {
         k_copy_status<<<1, 1, 0, s>>>(ptr, status);

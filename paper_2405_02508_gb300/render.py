@@ -6,6 +6,10 @@ for one mesh and a batch of views and chains the library calls:
     forward : mer_project -> mer_rasterize -> mer_shade
     backward: mer_backward (edge + interior) -> mer_project_backward
 
+With ``cover_hint`` (default) the rasterizer also writes the cover image (which facings cover each pixel
+centre, one byte a pixel) and the backward uses it to skip pixel pairs that cannot scatter; the results are
+the same without it.
+
 ``MerRender.apply(verts, attr, tex, cams, renderer, recompute_bary)`` exposes the
 same as an autograd function whose backward is the micro-edge kernel.  With
 ``recompute_bary`` the barycentric image is never stored (the backward always
@@ -22,7 +26,7 @@ from . import binding as B
 
 class Renderer:
     def __init__(self, tris: torch.Tensor, V: int, n_views: int, H: int, W: int, shading, C_attr: int,
-                 tex_shape=None, tile: int = 16, device: str = "cuda"):
+                 tex_shape=None, tile: int = 16, device: str = "cuda", cover_hint: bool = True):
         self.tris = tris.to(device=device, dtype=torch.int32).contiguous()
         self.T = int(self.tris.shape[0])
         self.V, self.n, self.H, self.W = int(V), int(n_views), int(H), int(W)
@@ -39,6 +43,7 @@ class Renderer:
         self.vpix = torch.empty((n, self.V, B.VERTEX_FLOATS), dtype=torch.float32, device=device)
         self.index = torch.empty((n, H, W), dtype=torch.int32, device=device)
         self.image = torch.empty((n, H, W, self.C), dtype=torch.float32, device=device)
+        self.cover = torch.empty((n, H, W), dtype=torch.uint8, device=device) if cover_hint else None
         self.grad_vpix = torch.zeros((n, self.V, 3), dtype=torch.float64, device=device)
         self.grad_verts = torch.zeros((self.V, 3), dtype=torch.float32, device=device)
         self._alloc_workspace(0)
@@ -55,13 +60,14 @@ class Renderer:
         B.mer_project_screen(scr.contiguous(), self.vpix)
 
     def rasterize(self, depth: torch.Tensor | None = None, bary: torch.Tensor | None = None, checked: bool = True):
-        B.mer_rasterize(self.vpix, self.tris, self.H, self.W, self.tile, self.workspace, self.index, depth, bary)
+        B.mer_rasterize(self.vpix, self.tris, self.H, self.W, self.tile, self.workspace, self.index, depth, bary,
+                        self.cover)
         if checked:
             code, total = B.mer_sync_status(self.workspace)
             if code == B.MER_EOVERFLOW:  # size the bin list exactly and redo
                 self._alloc_workspace(int(total * 1.25) + 1024)
                 B.mer_rasterize(self.vpix, self.tris, self.H, self.W, self.tile, self.workspace, self.index, depth,
-                                bary)
+                                bary, self.cover)
                 code, total = B.mer_sync_status(self.workspace)
             if code != B.MER_OK:
                 raise B.MerError(code, "mer_rasterize")
@@ -83,7 +89,7 @@ class Renderer:
             self.grad_vpix.zero_()
             self.grad_verts.zero_()
         B.mer_backward(self.vpix, self.tris, self.index, self.image, grad_image.contiguous(), attr.contiguous(), tex,
-                       self.sh, terms, self.grad_vpix, grad_attr, self.workspace)
+                       self.sh, terms, self.grad_vpix, grad_attr, self.workspace, self.cover)
         B.mer_project_backward(cams, self.vpix, self.grad_vpix, self.grad_verts)
         return self.grad_verts
 

@@ -41,7 +41,7 @@ class GpuResult:
 
 
 def gpu_run(scene, grad_images: np.ndarray, terms: int = 7, tile: int = 16, want_attr: bool = False,
-            store_bary: bool = True) -> GpuResult:
+            store_bary: bool = True, cover_hint: bool = True) -> GpuResult:
     import torch
 
     from paper_2405_02508_gb300 import binding as B
@@ -54,7 +54,7 @@ def gpu_run(scene, grad_images: np.ndarray, terms: int = 7, tile: int = 16, want
     tex = torch.from_numpy(scene.tex).to(dev) if scene.tex is not None else None
     n, H, W = scene.n_views, scene.H, scene.W
     r = Renderer(torch.from_numpy(scene.tris), len(scene.verts), n, H, W, scene.shading, scene.attr.shape[1],
-                 None if tex is None else tex.shape, tile=tile)
+                 None if tex is None else tex.shape, tile=tile, cover_hint=cover_hint)
     depth = torch.empty((n, H, W), dtype=torch.float32, device=dev)
     bary = torch.empty((n, H, W, 2), dtype=torch.float32, device=dev) if store_bary else None
     r.forward(verts, cams, attr, tex, depth=depth, bary=bary)

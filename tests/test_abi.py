@@ -48,7 +48,7 @@ def test_host_only_calls():
     assert lib.mer_workspace_size(100, 200, 2, 64, 48, 16, 0) > 0
     assert lib.mer_workspace_size(100, 200, 2, 64, 48, 12, 0) == 0
     assert lib.mer_workspace_size(100, 200, 2, 9000, 48, 16, 0) == 0
-    assert lib.mer_rasterize(None, 3, None, 1, 1, 16, 16, 16, None, 0, None, None, None, None) == binding.MER_EINVAL
+    assert lib.mer_rasterize(None, 3, None, 1, 1, 16, 16, 16, None, 0, None, None, None, None, None) == binding.MER_EINVAL
     assert lib.mer_project(None, 3, None, 1, None, None) == binding.MER_EINVAL
     assert lib.mer_project(None, 0, None, 1, None, None) == binding.MER_OK  # empty: nothing to do
 

@@ -42,8 +42,9 @@ def _cuda():
 
 
 def run_parity(orc, scene, grads, views=None, terms=ALL, tile=16, check_world=True, want_attr=False,
-               store_bary=True):
-    gpu = parity.gpu_run(scene, grads, terms=terms, tile=tile, want_attr=want_attr, store_bary=store_bary)
+               store_bary=True, cover_hint=True):
+    gpu = parity.gpu_run(scene, grads, terms=terms, tile=tile, want_attr=want_attr, store_bary=store_bary,
+                         cover_hint=cover_hint)
     views = list(range(scene.n_views)) if views is None else list(views)
     ovs = orc.render(scene, views)
     gs, gw, counts, ga = orc.backward_scene(scene, ovs, [grads[v] for v in views], views, mode=terms,
@@ -106,11 +107,12 @@ def test_parity_tiny_icosphere_l2(orc):
     assert stats[0]["covered"] > 5000
 
 
-@pytest.mark.parametrize("tile", [8, 16, 32])
-def test_parity_intersection_two_spheres(orc, tile):
-    """512^2, 2 x 20480 triangles interpenetrating: silhouettes and intersection micro-edges."""
+@pytest.mark.parametrize("tile,cover_hint", [(8, True), (16, True), (32, True), (16, False)])
+def test_parity_intersection_two_spheres(orc, tile, cover_hint):
+    """512^2, 2 x 20480 triangles interpenetrating: silhouettes and intersection micro-edges (with and
+    without the cover image that lets the backward skip pairs that cannot scatter)."""
     sc = scenes.two_spheres()
-    gpu, stats, counts = run_parity(orc, sc, sc.upstream(), tile=tile)
+    gpu, stats, counts = run_parity(orc, sc, sc.upstream(), tile=tile, cover_hint=cover_hint)
     assert counts[0]["intersection"] > 50
 
 
@@ -333,10 +335,10 @@ def test_invalid_arguments_rejected():
     from paper_2405_02508_gb300 import binding as B
 
     lib = B.lib()
-    assert lib.mer_rasterize(None, 3, None, 1, 1, 16, 16, 16, None, 0, None, None, None, None) == B.MER_EINVAL
+    assert lib.mer_rasterize(None, 3, None, 1, 1, 16, 16, 16, None, 0, None, None, None, None, None) == B.MER_EINVAL
     assert lib.mer_workspace_size(3, 1, 1, 16, 16, 12, 0) == 0  # tile must be 8, 16 or 32
     ws = torch.zeros(1024, device="cuda")
-    assert lib.mer_rasterize(None, 3, None, 1, 1, 9000, 16, 16, B._ptr(ws), 4096, None, None, None, None) == B.MER_EINVAL
+    assert lib.mer_rasterize(None, 3, None, 1, 1, 9000, 16, 16, B._ptr(ws), 4096, None, None, None, None, None) == B.MER_EINVAL
 
 
 def test_recompute_bary_bitwise_identical():
