@@ -31,7 +31,15 @@ constexpr int kHW = kTW + 2, kHH = kTH + 2;
 constexpr int kThreads = 256;
 constexpr int kCtasPerSm = 6;                     // resident CTAs per SM: at most 42 registers a thread
 static_assert(kTW == 32 && kTH == kRows * kThreads / 32, "a warp spans the tile's width");
-constexpr int kSlots = 512;       // per-tile vertex table (a 32x16 tile touches ~20-100 vertices)
+// Per-tile triangle table: a 32x16 tile of the head-scale workloads holds ~20-80 triangles.  256 slots
+// (128 when attribute gradients or the exact-crossing buffers also take shared memory) keep six CTAs
+// resident with most of the SM's on-chip memory left to the L1 cache that serves the vertex, texel and image
+// gathers; a tile with more triangles sends the excess straight to global memory.
+template <int NA, bool EXACT>
+struct TriTable {
+    static constexpr int kBits = (NA > 0 || EXACT) ? 7 : 8;
+    static constexpr int kSlots = 1 << kBits;
+};
 
 struct BwdArgs {
     mer_shading sh;
@@ -66,17 +74,19 @@ __device__ __forceinline__ void tri_normal(const VRec r[3], float N[3]) {
     N[2] = diff_of_products(e[0][0], e[1][1], e[0][1], e[1][0]);
 }
 
-// Slot of vertex `vid` in the tile table, inserting it if needed; -1 if the table is full.
-__device__ __forceinline__ int table_slot(int* keys, int vid) {
-    unsigned h = ((unsigned)vid * 2654435761u) >> (32 - 9);
+// Slot of triangle `key` in the tile table of 2^BITS slots, inserting it if needed; -1 if the table is full.
+template <int BITS>
+__device__ __forceinline__ int table_slot(int* keys, int key) {
+    constexpr int kSlots = 1 << BITS;
+    unsigned h = ((unsigned)key * 2654435761u) >> (32 - BITS);
 #pragma unroll 1
     for (int probe = 0; probe < kSlots; ++probe) {
-        // a slot's key only ever changes from -1 to a vertex id within a tile: a key already seen is final
+        // a slot's key only ever changes from -1 to a triangle id within a tile: a key already seen is final
         int k = *reinterpret_cast<volatile int*>(keys + h);
-        if (k == vid) return (int)h;
+        if (k == key) return (int)h;
         if (k == -1) {
-            k = atomicCAS(keys + h, -1, vid);
-            if (k == -1 || k == vid) return (int)h;
+            k = atomicCAS(keys + h, -1, key);
+            if (k == -1 || k == key) return (int)h;
         }
         h = (h + 1) & (kSlots - 1);
     }
@@ -103,9 +113,11 @@ template <int NA, bool EXACT>
 struct BwdShared {
     int sidx[kHH][kHW];
     unsigned char scov[kHH][kHW];  // cover image of the tile and halo (when given)
-    int skey[kSlots];
-    float sval[kSlots][3];
-    float sattr[NA > 0 ? kSlots : 1][NA > 0 ? NA : 1];
+    static constexpr int kSlots = TriTable<NA, EXACT>::kSlots;
+    int skey[kSlots];                 // triangle id, -1 = free
+    int svid[kSlots][3];              // its vertex ids
+    float sval[kSlots][3][3];         // per vertex of the triangle: dL/d(x_s, y_s, zeta)
+    float sattr[NA > 0 ? kSlots : 1][3][NA > 0 ? NA : 1];
     float efrag[kTH][32][3];  // per row: edge-term fragment gradients returned to the pixel's lane
     float evert[EXACT ? kTH : 1][32][3][2];  // exact-crossing option: per pixel, (x, y) per triangle vertex
 };
@@ -307,14 +319,17 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
 
 template <int NA, bool EXACT>
 __device__ __forceinline__ void table_clear(BwdShared<NA, EXACT>& S) {
-    for (int i = threadIdx.x; i < kSlots; i += kThreads) {
+    for (int i = threadIdx.x; i < S.kSlots; i += kThreads) {
         S.skey[i] = -1;
-        S.sval[i][0] = 0.f;
-        S.sval[i][1] = 0.f;
-        S.sval[i][2] = 0.f;
-        if (NA > 0) {
 #pragma unroll
-            for (int j = 0; j < (NA > 0 ? NA : 1); ++j) S.sattr[i][j] = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            S.sval[i][k][0] = 0.f;
+            S.sval[i][k][1] = 0.f;
+            S.sval[i][k][2] = 0.f;
+            if (NA > 0) {
+#pragma unroll
+                for (int j = 0; j < (NA > 0 ? NA : 1); ++j) S.sattr[i][k][j] = 0.f;
+            }
         }
     }
 }
@@ -521,17 +536,19 @@ __device__ __forceinline__ void row_pass(const BItem& it, int tx, int ty, int ro
     const bool tail = lane == 31 || tnext != t;
     double* gvv = it.gv;
     if (tail && t >= 0 && any) {
+        // one slot per triangle: the runs of one row hold different triangles, so their adds do not contend
+        const int sl = table_slot<TriTable<NA, EXACT>::kBits>(S.skey, t);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const int sl = table_slot(S.skey, vid[k]);
             if (sl >= 0) {
-                atomicAdd(&S.sval[sl][0], c0[k]);
-                atomicAdd(&S.sval[sl][1], c1[k]);
-                atomicAdd(&S.sval[sl][2], c2[k]);
+                S.svid[sl][k] = vid[k];  // every writer of the slot writes the same ids
+                atomicAdd(&S.sval[sl][k][0], c0[k]);
+                atomicAdd(&S.sval[sl][k][1], c1[k]);
+                atomicAdd(&S.sval[sl][k][2], c2[k]);
                 if (NA > 0) {
 #pragma unroll
                     for (int j = 0; j < (NA > 0 ? NA : 1); ++j)
-                        if (j < A) atomicAdd(&S.sattr[sl][j], ca[k][j]);
+                        if (j < A) atomicAdd(&S.sattr[sl][k][j], ca[k][j]);
                 }
             } else {  // table full: straight to global memory
                 atomicAdd(gvv + 3 * (size_t)vid[k], (double)c0[k]);
@@ -564,24 +581,27 @@ __device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, Bw
     const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
     const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
     double* gvv = it.gv;
-    for (int i = threadIdx.x; i < kSlots; i += kThreads) {
-        const int v = S.skey[i];
-        if (v < 0) continue;
-        const float s0 = S.sval[i][0], s1 = S.sval[i][1], s2 = S.sval[i][2];
+    for (int i = threadIdx.x; i < S.kSlots; i += kThreads) {
+        if (S.skey[i] < 0) continue;
         S.skey[i] = -1;
-        S.sval[i][0] = 0.f;
-        S.sval[i][1] = 0.f;
-        S.sval[i][2] = 0.f;
-        if (s0 != 0.f) atomicAdd(gvv + 3 * (size_t)v, (double)s0);
-        if (s1 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 1, (double)s1);
-        if (s2 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 2, (double)s2);
-        if (NA > 0) {
 #pragma unroll
-            for (int j = 0; j < (NA > 0 ? NA : 1); ++j) {
-                if (j >= A) break;
-                const float sa = S.sattr[i][j];
-                S.sattr[i][j] = 0.f;
-                if (sa != 0.f) atomicAdd(it.gattr + (size_t)v * a.sh.C_attr + a0 + j, sa);
+        for (int k = 0; k < 3; ++k) {
+            const int v = S.svid[i][k];
+            const float s0 = S.sval[i][k][0], s1 = S.sval[i][k][1], s2 = S.sval[i][k][2];
+            S.sval[i][k][0] = 0.f;
+            S.sval[i][k][1] = 0.f;
+            S.sval[i][k][2] = 0.f;
+            if (s0 != 0.f) atomicAdd(gvv + 3 * (size_t)v, (double)s0);
+            if (s1 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 1, (double)s1);
+            if (s2 != 0.f) atomicAdd(gvv + 3 * (size_t)v + 2, (double)s2);
+            if (NA > 0) {
+#pragma unroll
+                for (int j = 0; j < (NA > 0 ? NA : 1); ++j) {
+                    if (j >= A) break;
+                    const float sa = S.sattr[i][k][j];
+                    S.sattr[i][k][j] = 0.f;
+                    if (sa != 0.f) atomicAdd(it.gattr + (size_t)v * a.sh.C_attr + a0 + j, sa);
+                }
             }
         }
     }
