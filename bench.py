@@ -112,8 +112,8 @@ class ClockSampler:
 # one k_backward_batch launch, from an ncu capture of the same workload at 4 views (inputs already larger than
 # L2), per pixel of the launch, with the sha256 of the kernel's sources they were taken on: a launch of n views
 # moves / issues n*H*W times these.  They are reported only while the sources are unchanged.
-BACKWARD_TRAFFIC = {"bytes_per_pixel": 26.4142, "warp_instructions_per_pixel": 41.3116,
-                    "sources_sha256": "c9272b0c07b99c693e5ed4c6630744c7c80fa3253f48c0f6972958d816c4a7c9",
+BACKWARD_TRAFFIC = {"bytes_per_pixel": 27.0163, "warp_instructions_per_pixel": 37.5540,
+                    "sources_sha256": "2b1cd1149b499e99f3d435802a3e91b320c9fb6832f318ac1739fda9288be278",
                     "profile": "profiles/ncu_k_backward_batch_head_4x1334x2048.md"}
 
 
