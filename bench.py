@@ -113,7 +113,7 @@ class ClockSampler:
 # L2), per pixel of the launch, with the sha256 of the kernel's sources they were taken on: a launch of n views
 # moves / issues n*H*W times these.  They are reported only while the sources are unchanged.
 BACKWARD_TRAFFIC = {"bytes_per_pixel": 27.0163, "warp_instructions_per_pixel": 37.5540,
-                    "sources_sha256": "2b1cd1149b499e99f3d435802a3e91b320c9fb6832f318ac1739fda9288be278",
+                    "sources_sha256": "c6198e8a2528908fef7d97d3e5ad4a5c0a4c78094f177d6ce9b06ad53287eb9e",
                     "profile": "profiles/ncu_k_backward_batch_head_4x1334x2048.md"}
 
 

@@ -12,11 +12,12 @@
 //     top -> dp/dr = 1 on the pair axis) or Eq. 12 (intersection) for p's side.
 // The fragment gradient is gathered to the 3 vertices with p's screen
 // barycentrics (dL/dv_i = lambda_i dL/dr).  A warp first classifies the edge
-// pairs of both its rows together (they rarely fill more than one 32-lane pass),
-// then takes its rows one at a time: the 9 per-pixel vertex terms are summed over
-// each run of equal triangle id in the row (segmented shuffle scan, FP32), then
-// per vertex in a shared-memory table (FP32), and the tile's per-vertex totals go
-// to grad_vpix with one FP64 atomic per component.
+// pairs of both its rows together (they rarely fill more than one 32-lane pass;
+// with the rasterizer's cover image, only the pairs it does not rule out), then
+// takes its rows one at a time: the 9 per-pixel vertex terms are summed over each
+// run of equal triangle id in the row (segmented shuffle scan, FP32), then per
+// triangle in a shared-memory table (FP32), and the flush adds each triangle's
+// totals to its 3 vertices in grad_vpix with one FP64 atomic per component.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -313,7 +314,7 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
 }
 
 // A tile's work is split in three phases separated by CTA barriers: tile_halo (index tile + halo into shared
-// memory), tile_compute (every pixel's gradients, aggregated into the vertex table) and tile_flush (table to
+// memory), tile_compute (every pixel's gradients, aggregated into the triangle table) and tile_flush (table to
 // global memory, slots cleared for the next tile).  The table starts clear (table_clear once per CTA), and a
 // persistent CTA overlaps the flush of one tile with the halo load of the next.
 

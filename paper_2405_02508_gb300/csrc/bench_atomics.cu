@@ -1,6 +1,6 @@
 // bench_atomics.cu -- a standalone measurement of the atomic throughputs the backward and raster kernels
 // depend on, for their atomic rooflines: global FP64 / FP32 reductions into an L2-resident array (the
-// vertex-gradient flush), and shared-memory adds of FP32, int32, FP64 and u64 (the per-tile vertex table,
+// vertex-gradient flush), and shared-memory adds of FP32, int32, FP64 and u64 (the per-tile triangle table,
 // the z-buffer) without and with address conflicts.  Not part of the library.
 //
 //   nvcc -gencode arch=compute_103a,code=sm_103a -O3 paper_2405_02508_gb300/csrc/bench_atomics.cu -o bench_atomics
