@@ -59,7 +59,8 @@ def test_batch_equals_multiview_renderer(tile):
 @pytest.mark.parametrize("tile", [16, 64])
 def test_fused_render_equals_raster_then_shade(tile):
     """mer_batch_render (raster + shade in one pass) writes the same index, depth, barycentrics and image as
-    mer_batch_rasterize followed by mer_batch_shade, bit for bit; also with interpolated attributes."""
+    mer_batch_rasterize followed by mer_batch_shade, bit for bit, and the same cover image; also with
+    interpolated attributes."""
     import torch
 
     from paper_2405_02508_gb300.batch import BatchRenderer
@@ -75,10 +76,11 @@ def test_fused_render_equals_raster_then_shade(tile):
         bary = torch.full((P, 2), -7.0, device="cuda")
         br.index.fill_(-9)
         br.image.fill_(-9.0)
+        br.cover.fill_(255)
         br.forward(verts, attr, tex, depth, bary, fused=fused)
         br.check()
-        out[fused] = (br.index.clone(), br.image.clone(), depth, bary)
-    for a, b in zip(out[False], out[True]):
+        out[fused] = (br.index.clone(), br.image.clone(), depth, bary, br.cover.clone())
+    for a, b in zip(out[False], out[True]):  # the cover image too
         assert torch.equal(a, b)
     its = scenes.uneven_batch(n_items=5, t_max=20000, resolutions=(96, 200))
     br2 = BatchRenderer([(it.verts, it.tris) for it in its], [(k, k, it.H, it.W) for k, it in enumerate(its)],
