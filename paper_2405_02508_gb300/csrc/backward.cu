@@ -32,13 +32,13 @@ constexpr int kHW = kTW + 2, kHH = kTH + 2;
 constexpr int kThreads = 256;
 constexpr int kCtasPerSm = 6;                     // resident CTAs per SM: at most 42 registers a thread
 static_assert(kTW == 32 && kTH == kRows * kThreads / 32, "a warp spans the tile's width");
-// Per-tile triangle table: a 32x16 tile of the head-scale workloads holds ~20-80 triangles.  256 slots
-// (128 when attribute gradients or the exact-crossing buffers also take shared memory) keep six CTAs
-// resident with most of the SM's on-chip memory left to the L1 cache that serves the vertex, texel and image
-// gathers; a tile with more triangles sends the excess straight to global memory.
+// Per-tile triangle table: a 32x16 tile of the head-scale workloads holds ~20-80 triangles.  128 slots keep
+// six CTAs resident with most of the SM's on-chip memory left to the L1 cache that serves the vertex, texel
+// and image gathers (256 slots measured 2.7 % slower on the multi-view head workload); a tile with more
+// triangles sends the excess straight to global memory.
 template <int NA, bool EXACT>
 struct TriTable {
-    static constexpr int kBits = (NA > 0 || EXACT) ? 7 : 8;
+    static constexpr int kBits = 7;
     static constexpr int kSlots = 1 << kBits;
 };
 
