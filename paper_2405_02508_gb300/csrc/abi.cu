@@ -38,7 +38,7 @@ extern "C" int mer_launch_shade_batch(const mer_vertex*, const int*, const mer_i
                                       cudaStream_t);
 extern "C" int mer_launch_backward_batch(const mer_vertex*, const int*, const mer_item*, int, long long, const int*,
                                          const unsigned char*, const float*, const float*, const float*,
-                                         const float*, const mer_shading*, int, double*, float*, void*, int,
+                                         const float*, const mer_shading*, int, double*, float*, void*, int, double,
                                          cudaStream_t);
 
 namespace {
@@ -317,7 +317,8 @@ int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_it
     if (grad_attr && sh->uv_offset < 0 && sh->n_main > 4) return MER_EINVAL;  // attribute gradients: <= 4 channels
     if (!workspace || !aligned256(workspace) || persistent_ctas < 0) return MER_EINVAL;
     return mer_launch_backward_batch(vpix, tris, items, t->n_items, t->btiles, index, cover, image, grad_image, attr,
-                                     tex, sh, terms, grad_vpix, grad_attr, workspace, persistent_ctas, S(stream));
+                                     tex, sh, terms, grad_vpix, grad_attr, workspace, persistent_ctas,
+                                     (double)t->trecs / (double)t->pixels, S(stream));
 }
 
 int mer_batch_project_backward(const mer_camera* cams, const mer_item* items, const mer_batch_totals* t,

@@ -32,13 +32,16 @@ constexpr int kHW = kTW + 2, kHH = kTH + 2;
 constexpr int kThreads = 256;
 constexpr int kCtasPerSm = 6;                     // resident CTAs per SM: at most 42 registers a thread
 static_assert(kTW == 32 && kTH == kRows * kThreads / 32, "a warp spans the tile's width");
-// Per-tile triangle table: a 32x16 tile of the head-scale workloads holds ~20-80 triangles.  128 slots keep
-// six CTAs resident with most of the SM's on-chip memory left to the L1 cache that serves the vertex, texel
-// and image gathers (256 slots measured 2.7 % slower on the multi-view head workload); a tile with more
-// triangles sends the excess straight to global memory.
-template <int NA, bool EXACT>
+// Per-tile triangle table of 2^BITS slots: a 32x16 tile of the head-scale workloads holds ~20-80 triangles.
+// 128 slots keep six CTAs resident with most of the SM's on-chip memory left to the L1 cache that serves the
+// vertex, texel and image gathers (256 slots measured 2.7 % slower on the multi-view head workload); a tile
+// with more triangles sends the excess straight to global memory, so launches whose meshes are dense on
+// screen (more than 0.1 triangle per pixel) take 256 slots.
+constexpr int kTableBits = 7, kTableBitsDense = 8;
+constexpr double kDenseTrianglesPerPixel = 0.1;
+template <int NA, bool EXACT, int BITS>
 struct TriTable {
-    static constexpr int kBits = 7;
+    static constexpr int kBits = BITS;
     static constexpr int kSlots = 1 << kBits;
 };
 
@@ -110,11 +113,11 @@ struct BItem {
 
 constexpr int kMaxA = 4;  // most attribute-gradient channels carried through the per-tile aggregation
 
-template <int NA, bool EXACT>
+template <int NA, bool EXACT, int BITS>
 struct BwdShared {
     int sidx[kHH][kHW];
     unsigned char scov[kHH][kHW];  // cover image of the tile and halo (when given)
-    static constexpr int kSlots = TriTable<NA, EXACT>::kSlots;
+    static constexpr int kSlots = TriTable<NA, EXACT, BITS>::kSlots;
     int skey[kSlots];                 // triangle id, -1 = free
     int svid[kSlots][3];              // its vertex ids
     float sval[kSlots][3][3];         // per vertex of the triangle: dL/d(x_s, y_s, zeta)
@@ -129,8 +132,8 @@ struct BwdShared {
 // classified 32 at a time; a pair whose source fragment scatters adds into that pixel's slot of the per-row
 // shared buffer efrag (evert for the exact-crossing option), read back by the pixel's lane in its row pass.
 // Returns false when the rows hold no pair (the buffers are then not written).
-template <int NA, bool EXACT>
-__device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, BwdShared<NA, EXACT>& S, void* ws,
+template <int NA, bool EXACT, int BITS>
+__device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, BwdShared<NA, EXACT, BITS>& S, void* ws,
                                           int r0, int lane, int x0, int y0) {
     const unsigned full = 0xffffffffu;
     const int C = a.sh.C;
@@ -318,8 +321,8 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
 // global memory, slots cleared for the next tile).  The table starts clear (table_clear once per CTA), and a
 // persistent CTA overlaps the flush of one tile with the halo load of the next.
 
-template <int NA, bool EXACT>
-__device__ __forceinline__ void table_clear(BwdShared<NA, EXACT>& S) {
+template <int NA, bool EXACT, int BITS>
+__device__ __forceinline__ void table_clear(BwdShared<NA, EXACT, BITS>& S) {
     for (int i = threadIdx.x; i < S.kSlots; i += kThreads) {
         S.skey[i] = -1;
 #pragma unroll
@@ -336,8 +339,8 @@ __device__ __forceinline__ void table_clear(BwdShared<NA, EXACT>& S) {
 }
 
 // Returns whether this thread loaded a covered pixel of the tile itself (not the halo).
-template <int NA, bool EXACT>
-__device__ __forceinline__ bool tile_halo(const BItem& it, int tx, int ty, BwdShared<NA, EXACT>& S) {
+template <int NA, bool EXACT, int BITS>
+__device__ __forceinline__ bool tile_halo(const BItem& it, int tx, int ty, BwdShared<NA, EXACT, BITS>& S) {
     bool covered = false;
     for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
         const int hy = i / kHW, hx = i % kHW;
@@ -355,9 +358,9 @@ __device__ __forceinline__ bool tile_halo(const BItem& it, int tx, int ty, BwdSh
 // the row's edge buffers).
 // NA > 0: also produce the attribute gradients (channels [a0, a0 + NA) of each vertex's attribute row, NA <= 4:
 // the interpolated channels, or (u, v) in texture mode), aggregated like the vertex gradients.
-template <int NA, bool EXACT>
+template <int NA, bool EXACT, int BITS>
 __device__ __forceinline__ void row_pass(const BItem& it, int tx, int ty, int row, int lane, bool pairs,
-                                         const BwdArgs& a, const float* __restrict__ tex, BwdShared<NA, EXACT>& S,
+                                         const BwdArgs& a, const float* __restrict__ tex, BwdShared<NA, EXACT, BITS>& S,
                                          void* ws) {
     const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
     const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
@@ -538,7 +541,7 @@ __device__ __forceinline__ void row_pass(const BItem& it, int tx, int ty, int ro
     double* gvv = it.gv;
     if (tail && t >= 0 && any) {
         // one slot per triangle: the runs of one row hold different triangles, so their adds do not contend
-        const int sl = table_slot<TriTable<NA, EXACT>::kBits>(S.skey, t);
+        const int sl = table_slot<TriTable<NA, EXACT, BITS>::kBits>(S.skey, t);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             if (sl >= 0) {
@@ -567,18 +570,18 @@ __device__ __forceinline__ void row_pass(const BItem& it, int tx, int ty, int ro
 
 // The tile (tx, ty) of an item, after tile_halo and a barrier: each warp takes rows kRows * warp ..
 // kRows * warp + kRows - 1, first their edge pairs together, then each row's pixels.
-template <int NA, bool EXACT>
+template <int NA, bool EXACT, int BITS>
 __device__ __forceinline__ void tile_compute(const BItem& it, int tx, int ty, const BwdArgs& a,
-                                             const float* __restrict__ tex, BwdShared<NA, EXACT>& S, void* ws) {
+                                             const float* __restrict__ tex, BwdShared<NA, EXACT, BITS>& S, void* ws) {
     const int lane = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * kRows;
-    const bool pairs = (a.terms & MER_EDGE) && edge_rows<NA, EXACT>(it, a, S, ws, r0, lane, tx * kTW, ty * kTH);
+    const bool pairs = (a.terms & MER_EDGE) && edge_rows<NA, EXACT, BITS>(it, a, S, ws, r0, lane, tx * kTW, ty * kTH);
 #pragma unroll 1
-    for (int k = 0; k < kRows; ++k) row_pass<NA, EXACT>(it, tx, ty, r0 + k, lane, pairs, a, tex, S, ws);
+    for (int k = 0; k < kRows; ++k) row_pass<NA, EXACT, BITS>(it, tx, ty, r0 + k, lane, pairs, a, tex, S, ws);
 }
 
 // After tile_compute and a barrier: add the table to global memory and clear it.
-template <int NA, bool EXACT>
-__device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, BwdShared<NA, EXACT>& S) {
+template <int NA, bool EXACT, int BITS>
+__device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, BwdShared<NA, EXACT, BITS>& S) {
     const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
     const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
     double* gvv = it.gv;
@@ -608,7 +611,7 @@ __device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, Bw
     }
 }
 
-template <int NA, bool EXACT>
+template <int NA, bool EXACT, int BITS>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward(const mer_vertex* __restrict__ vpix, const int* __restrict__ tris,
                                                        const int* __restrict__ index,
                                                        const unsigned char* __restrict__ cover,
@@ -617,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward(const mer_ver
                                                        const float* __restrict__ tex, BwdArgs a,
                                                        double* __restrict__ grad_vpix, float* __restrict__ grad_attr,
                                                        void* ws) {
-    __shared__ BwdShared<NA, EXACT> S;
+    __shared__ BwdShared<NA, EXACT, BITS> S;
     const int tiles_per_view = a.ntx * a.nty;
     const int view = blockIdx.x / tiles_per_view;
     const int local = blockIdx.x % tiles_per_view;
@@ -636,13 +639,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward(const mer_ver
     table_clear(S);
     const bool covered = tile_halo(it, local % a.ntx, local / a.ntx, S);
     if (!__syncthreads_or(covered)) return;  // background tile
-    tile_compute<NA, EXACT>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
+    tile_compute<NA, EXACT, BITS>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
     __syncthreads();
     tile_flush(it, a, S);
 }
 
 // Persistent: each CTA takes the next backward tile of any item from the work queue.
-template <int NA, bool EXACT>
+template <int NA, bool EXACT, int BITS>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward_batch(const mer_vertex* __restrict__ vpix,
                                                              const int* __restrict__ tris,
                                                              const mer_item* __restrict__ items, int n_items,
@@ -654,7 +657,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward_batch(const m
                                                              const float* __restrict__ tex, BwdArgs a,
                                                              double* __restrict__ grad_vpix,
                                                              float* __restrict__ grad_attr, void* ws) {
-    __shared__ BwdShared<NA, EXACT> S;
+    __shared__ BwdShared<NA, EXACT, BITS> S;
     __shared__ long long s_tile;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     const int C = a.sh.C, Ca = a.sh.C_attr;
@@ -695,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward_batch(const m
         tile_halo(it, tx, ty, S);
         __syncthreads();
         if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_backward, 1ull);
-        tile_compute<NA, EXACT>(it, tx, ty, a, tex, S, ws);
+        tile_compute<NA, EXACT, BITS>(it, tx, ty, a, tex, S, ws);
         __syncthreads();
         tile_flush(it, a, S);
     }
@@ -719,7 +722,7 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
                                          long long btiles, const int* index, const unsigned char* cover,
                                          const float* image, const float* grad_image, const float* attr, const float* tex,
                                          const mer_shading* sh, int terms, double* grad_vpix, float* grad_attr,
-                                         void* ws, int persistent_ctas, cudaStream_t s) {
+                                         void* ws, int persistent_ctas, double tris_per_pixel, cudaStream_t s) {
     if (btiles == 0) return 0;
     BwdArgs a;
     a.sh = *sh;
@@ -735,17 +738,25 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
         int per_sm = 0, sms = 0, dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 2;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 2;
-        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_batch<0, false>,
-                                                                            kThreads, 0);
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_backward_batch<0, false, kTableBits>, kThreads, 0);
         if (e != cudaSuccess) return 2;
         grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
     }
     const bool exact = (terms & MER_EXACT_CROSSING) != 0;
 #define MER_BWD_BATCH(A, E)                                                                                        \
-    k_backward_batch<A, E><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, cover, image, grad_image, \
+    k_backward_batch<A, E, kTableBits><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, cover, image, grad_image, \
                                                      attr, tex, a, grad_vpix, grad_attr, ws)
+    const bool dense = tris_per_pixel > kDenseTrianglesPerPixel;
     switch (attr_channels(sh, grad_attr) * 2 + (exact ? 1 : 0)) {
-        case 0: MER_BWD_BATCH(0, false); break;
+        case 0:
+            if (dense)
+                k_backward_batch<0, false, kTableBitsDense><<<grid, kThreads, 0, s>>>(
+                    vpix, tris, items, n_items, btiles, index, cover, image, grad_image, attr, tex, a, grad_vpix,
+                    grad_attr, ws);
+            else
+                MER_BWD_BATCH(0, false);
+            break;
         case 1: MER_BWD_BATCH(0, true); break;
         case 2: MER_BWD_BATCH(1, false); break;
         case 3: MER_BWD_BATCH(1, true); break;
@@ -777,10 +788,17 @@ extern "C" int mer_launch_backward(const mer_vertex* vpix, int V, const int* tri
     if (blocks == 0) return 0;
     const bool exact = (terms & MER_EXACT_CROSSING) != 0;
 #define MER_BWD(A, E)                                                                                             \
-    k_backward<A, E><<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, cover, image, grad_image, attr, tex, a, \
+    k_backward<A, E, kTableBits><<<(unsigned)blocks, kThreads, 0, s>>>(vpix, tris, index, cover, image, grad_image, attr, tex, a, \
                                                            grad_vpix, grad_attr, ws)
+    const bool dense = (double)T > kDenseTrianglesPerPixel * (double)H * (double)W;
     switch (attr_channels(sh, grad_attr) * 2 + (exact ? 1 : 0)) {
-        case 0: MER_BWD(0, false); break;
+        case 0:
+            if (dense)
+                k_backward<0, false, kTableBitsDense><<<(unsigned)blocks, kThreads, 0, s>>>(
+                    vpix, tris, index, cover, image, grad_image, attr, tex, a, grad_vpix, grad_attr, ws);
+            else
+                MER_BWD(0, false);
+            break;
         case 1: MER_BWD(0, true); break;
         case 2: MER_BWD(1, false); break;
         case 3: MER_BWD(1, true); break;
