@@ -125,3 +125,29 @@ def lambda_gradients(P2):
     M = np.array([[P2[0, 0], P2[1, 0], P2[2, 0]], [P2[0, 1], P2[1, 1], P2[2, 1]], [1.0, 1.0, 1.0]])
     Minv = np.linalg.inv(M)
     return Minv, Minv[:, :2]
+
+
+def perspective_weights(P3, px, py):
+    """Perspective-correct barycentrics of the camera-space point seen at pixel (px, py), by a direct solve.
+
+    ``P3`` [3,3] holds (x_s, y_s, zeta) of the triangle's vertices.  The point sum_i b_i X_i (camera space,
+    sum_i b_i = 1) projects to (px, py) iff sum_i b_i Z_i (x_i - px) = 0 and sum_i b_i Z_i (y_i - py) = 0,
+    Z_i = 1 / zeta_i: three linear equations in b.  Returns (b [3], depth = sum_i b_i Z_i).
+    """
+    Z = 1.0 / P3[:, 2]
+    A = np.array([Z * (P3[:, 0] - px), Z * (P3[:, 1] - py), np.ones(3)])
+    b = np.linalg.solve(A, np.array([0.0, 0.0, 1.0]))
+    return b, float(b @ Z)
+
+
+def projection_jacobian_fd(verts, cam, h=1e-4):
+    """d(x_s, y_s, zeta)/d(world position) [V,3,3] by fourth-order central differences of
+    ``project_homogeneous`` (row = output, column = world axis)."""
+    v = np.asarray(verts, np.float64)
+    J = np.zeros((len(v), 3, 3))
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        f = [project_homogeneous(v + k * e, cam) for k in (-2, -1, 1, 2)]
+        J[:, :, a] = (f[0] - 8 * f[1] + 8 * f[2] - f[3]) / (12 * h)
+    return J

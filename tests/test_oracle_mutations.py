@@ -36,6 +36,12 @@ MUTATIONS = {
     "crossing_weight_order": ("wout[0] = 1.0 - u; wout[1] = u;", "wout[0] = u; wout[1] = 1.0 - u;"),
     "crossing_first_edge": ("(__int128)eF * bden < (__int128)bnum * (eF - eO)",
                             "(__int128)eF * bden > (__int128)bnum * (eF - eO)"),
+    "pixel_depth_reciprocal": ("Z = 1.0 / s;", "Z = s;"),
+    "pixel_bary_screen_linear": ("for (int i = 0; i < 3; ++i) b[i] = lam[i] * scr[3 * tri[i] + 2] / s;",
+                                 "for (int i = 0; i < 3; ++i) b[i] = lam[i];"),
+    "texel_eps_too_small": ("double eps = n * 32.0 * ulp * ext", "double eps = n * 2.0 * ulp * ext"),
+    "texel_clamp_edge": ("amb = fabs(xc) <= eps || fabs(xc - (n - 1)) <= eps ||",
+                         "amb = fabs(xc - (n - 1)) <= eps ||"),
     "project_backward_transpose": ("grad_verts[3 * v + 0] += R[0] * gX + R[3] * gY + R[6] * gZ;",
                                    "grad_verts[3 * v + 0] += R[0] * gX + R[1] * gY + R[2] * gZ;"),
 }

@@ -779,3 +779,162 @@ def test_exact_crossing_weights_equal_brute_force_derivatives(orc):
                         assert fd == pytest.approx(w[k], abs=1e-5), (trial, x, y, axis, k, fd, w)
                     checked += 1
     assert checked > 200
+
+
+# ---------------------------------------------------------------------------
+# pixel values (barycentrics module): screen barycentrics, perspective-correct barycentrics, depth
+# ---------------------------------------------------------------------------
+
+def test_pixel_values_match_direct_solves(orc):
+    """Each covered pixel's screen barycentrics solve [x; y; 1] lam = [px; py; 1]; its perspective-correct
+    weights b are the affine weights of the camera-space point on the pixel ray (a direct 3x3 solve, see
+    ``geom.perspective_weights``); its depth is that point's Z, and also 1 / zeta of the plane through the
+    vertices in (x_s, y_s, zeta) (zeta = 1/Z is affine on screen).  Background pixels hold zeros."""
+    rng = np.random.default_rng(41)
+    H, W = 20, 26
+    nt = 10
+    V2 = rng.uniform(-6, 32, (3 * nt, 2))
+    zeta = rng.uniform(0.15, 0.9, 3 * nt)  # strongly varying depth across each triangle
+    scr = np.concatenate([V2, zeta[:, None]], axis=1)
+    T = np.arange(3 * nt, dtype=np.int32).reshape(nt, 3)
+    scr, snap, flags = orc.snap_screen(scr)
+    index, _, _ = orc.rasterize(scr, snap, flags, T, H, W)
+    lam, bary, depth = orc.pixel_values(scr, T, index)
+    checked = 0
+    for y in range(H):
+        for x in range(W):
+            t = index[y, x]
+            if t < 0:
+                assert np.all(lam[y, x] == 0) and np.all(bary[y, x] == 0) and depth[y, x] == 0
+                continue
+            P3 = scr[T[t]]
+            px, py = x + 0.5, y + 0.5
+            M = np.array([P3[:, 0], P3[:, 1], np.ones(3)])
+            lam_ref = np.linalg.solve(M, np.array([px, py, 1.0]))
+            b_ref, Z_ref = geom.perspective_weights(P3, px, py)
+            plane = np.linalg.solve(np.array([P3[:, 0], P3[:, 1], np.ones(3)]).T, P3[:, 2])
+            Z_plane = 1.0 / (plane @ np.array([px, py, 1.0]))
+            np.testing.assert_allclose(lam[y, x], lam_ref, rtol=1e-9, atol=1e-11)
+            np.testing.assert_allclose(bary[y, x], b_ref, rtol=1e-9, atol=1e-11)
+            assert depth[y, x] == pytest.approx(Z_ref, rel=1e-11)
+            assert depth[y, x] == pytest.approx(Z_plane, rel=1e-11)
+            checked += 1
+    assert checked > 150
+
+
+# ---------------------------------------------------------------------------
+# texel-cell ambiguity flags (test helper): brute-force FP32 evaluations of the texel coordinate
+# ---------------------------------------------------------------------------
+
+def _fp32_texel_coords(b, uk, N, rel_ulps, rng, draws):
+    """Texel coordinate x = u N - 1/2 of u = sum_k b_k u_k as an FP32 evaluation forms it: the base
+    x_0 = u_0 N - 1/2 (exact for N a power of two), the offset sum_{k=1,2} b_k (x_k - x_0) in FP32 with
+    b_k carrying a relative error of up to ``rel_ulps`` ulps, added to the fraction of x_0 (the integer part
+    split off exactly).  Returns the cells floor(x) of ``draws`` evaluations with random errors and of the
+    four extreme sign patterns, [npix, draws + 4]."""
+    f32 = np.float32
+    ulp = f32(2.0 ** -24)
+    x = (uk.astype(f32) * f32(N) - f32(0.5)).astype(f32)  # [npix, 3], exact
+    xb = x[:, 0]
+    fl = np.floor(xb)
+    base = (xb - fl).astype(f32)
+    pats = [rng.uniform(-1, 1, (len(b), 2)) for _ in range(draws)]
+    pats += [np.tile(np.array(s, float), (len(b), 1)) for s in ((1, 1), (1, -1), (-1, 1), (-1, -1))]
+    cells = []
+    for p in pats:
+        b1 = (b[:, 1] * (1.0 + rel_ulps * float(ulp) * p[:, 0])).astype(f32)
+        b2 = (b[:, 2] * (1.0 + rel_ulps * float(ulp) * p[:, 1])).astype(f32)
+        d = (b1 * (x[:, 1] - xb).astype(f32)).astype(f32) + (b2 * (x[:, 2] - xb).astype(f32)).astype(f32)
+        f = (base + d.astype(f32)).astype(f32)
+        cells.append(fl + np.floor(f.astype(np.float64)))
+    return np.stack(cells, axis=1)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_texel_ambiguity_flags_every_pixel_an_fp32_evaluation_can_move(orc, axis):
+    """Two large triangles at constant depth (so b = lambda, affine on screen) carry uv such that the texel
+    coordinate along ``axis`` is the pixel's own coordinate (minus a shift, so that on the v axis some rows
+    sit on the clamp edges 0 and n - 1) plus delta, a tiny offset that grows along the other screen axis:
+    many pixels lie close to a texel-cell boundary.  Each pixel whose cell (on v: the clamp state) changes
+    under some FP32 evaluation of the texel coordinate (barycentric errors up to 16 ulps, FP32 operations)
+    must be flagged; pixels whose offset is far beyond the flag's bound must not be."""
+    H, W, N = 48, 44, 32
+    shift = 0.0 if axis == 0 else 10.0
+    big = 4.0 * max(H, W)
+    scr = np.array([[0.0, 0.0, 0.5], [big, 0.0, 0.5], [0.0, big, 0.5], [big, big, 0.5]])
+    T = np.array([[0, 1, 2], [1, 3, 2]], np.int32)
+    scr, snap, flags = orc.snap_screen(scr)
+    index, _, _ = orc.rasterize(scr, snap, flags, T, H, W)
+    assert np.all(index >= 0)
+    other = 1 - axis
+    n_other = W if other == 0 else H
+    alpha = 1e-5  # delta per pixel along the other axis; zero in the middle
+    # texel coordinate along `axis`: P_axis - 1/2 - shift + alpha (P_other - n_other / 2)  (u = (coord + 1/2) / N)
+    a = np.zeros((4, 2), np.float32)
+    for v in range(4):
+        coord = scr[v, axis] - 0.5 - shift + alpha * (scr[v, other] - n_other / 2)
+        a[v, axis] = np.float32((coord + 0.5) / N)
+        a[v, other] = np.float32((N // 2 + 0.25) / N)
+    sh = Shading(n_main=3, C=3, uv_offset=0, bg=[0, 0, 0])
+    tex = np.zeros((N, N, 4), np.float32)
+    flagged = orc.texel_ambiguity(scr, T, index, a, sh, tex)
+    ys, xs = np.mgrid[0:H, 0:W]
+    b = np.zeros((H * W, 3))
+    uk = np.zeros((H * W, 3))
+    for i, (y, x) in enumerate(zip(ys.ravel(), xs.ravel())):
+        t = index[y, x]
+        M = np.array([scr[T[t], 0], scr[T[t], 1], np.ones(3)])
+        b[i] = np.linalg.solve(M, np.array([x + 0.5, y + 0.5, 1.0]))
+        uk[i] = a[T[t], axis]
+    cells = _fp32_texel_coords(b, uk, N, 16.0, np.random.default_rng(7), 16)
+    exact_x = (b * uk.astype(np.float64)).sum(axis=1) * N - 0.5
+    exact = np.floor(exact_x)
+    if axis == 1:  # v clamps: only the clamp state and the interior cell matter
+        cells = np.clip(cells, -1, N - 1)
+        exact = np.clip(exact, -1, N - 1)
+    must = (cells != exact[:, None]).any(axis=1).reshape(H, W)
+    assert must.sum() > 30, "the offsets should put many pixels within FP32 reach of a boundary"
+    if axis == 1:
+        near_low = np.abs(exact_x) < 2e-5
+        assert (must.ravel() & near_low).any(), "some pixel must sit on the lower clamp edge"
+    missed = must & ~flagged
+    assert missed.sum() == 0, f"{int(missed.sum())} pixels can change cell but are not flagged"
+    delta = np.abs(exact_x - np.rint(exact_x)).reshape(H, W)
+    far = delta > 1.5e-4
+    assert far.sum() > 100 and not flagged[far].any(), "pixels far from every boundary are flagged"
+
+
+def test_texel_ambiguity_share_on_head_scale_view_is_small(orc):
+    """On a textured head-scale view the flags touch a small share of the covered pixels (they exclude
+    triangles from the gradient comparison, so their share bounds what the parity tests leave out)."""
+    sc = scenes.head_single_view(H=256, W=256, n=64, tex_size=512)
+    ov = orc.render(sc)[0]
+    cov = ov.index >= 0
+    share = ov.texamb[cov].mean()
+    assert cov.sum() > 20000
+    assert share < 2e-3, share
+
+
+# ---------------------------------------------------------------------------
+# world-space conditioning sums (test helper of the parity bound)
+# ---------------------------------------------------------------------------
+
+def test_world_condition_matches_finite_difference_jacobian(orc):
+    """oracle.world_condition pushes per-view magnitude sums through |R^T J^T|; with J taken by finite
+    differences of an independent homogeneous projection, the same sums agree, and they bound the world
+    gradient of any per-view gradient whose magnitudes they are."""
+    sc = scenes.head_multiview(n_views=3, H=64, W=48, n=8)
+    views = [0, 1, 2]
+    ovs = orc.render(sc, views)
+    rng = np.random.default_rng(5)
+    S_views = [np.abs(rng.standard_normal((len(sc.verts), 3))) for _ in views]
+    Sw = orc.world_condition(sc, views, ovs, S_views)
+    ref = np.zeros_like(Sw)
+    gw = np.zeros_like(Sw)
+    for k, v in enumerate(views):
+        J = geom.projection_jacobian_fd(sc.verts, sc.cams[v])  # d(screen)/d(world)
+        ref += np.einsum("vkj,vk->vj", np.abs(J), S_views[k])
+        g = S_views[k] * rng.choice([-1.0, 1.0], S_views[k].shape)
+        gw += orc.project_backward(sc.verts, sc.cams[v], g)
+    np.testing.assert_allclose(Sw, ref, rtol=1e-6, atol=1e-9)
+    assert np.all(np.abs(gw) <= Sw * (1 + 1e-9) + 1e-12)
