@@ -44,7 +44,8 @@ enum {
     MER_EINVAL = 1,    /* bad argument (null pointer, size out of range, bad option) */
     MER_ECUDA = 2,     /* a CUDA launch or runtime call failed */
     MER_EOVERFLOW = 3, /* the bin list did not fit in the workspace (mer_sync_status) */
-    MER_ERANGE = 4     /* a triangle or index-image entry was out of range (mer_sync_status) */
+    MER_ERANGE = 4,    /* a triangle or index-image entry was out of range (mer_sync_status) */
+    MER_EFIXED = 5     /* a contribution exceeded the fixed-point range of MER_DETERMINISTIC (mer_sync_status) */
 };
 
 /* Pinhole camera, OpenCV convention (+X right, +Y down, +Z forward), 136 bytes.
@@ -94,6 +95,12 @@ typedef struct mer_shading {
     int backface_ch; /* channel of the back-face image (Supp. B): 1 where the visible triangle faces away
                         from the camera (snapped screen area > 0 with y down), 0 elsewhere; or -1.  It is
                         constant per triangle, so only the edge term differentiates it. */
+    int precise;     /* 0: FP32 shading arithmetic.  1: every shaded value is evaluated in FP64 from the FP32
+                        inputs and rounded once to FP32, so the image is the correctly rounded value up to FP64
+                        rounding (bit-reproducible against any FP64 evaluation of the same definition, except
+                        where the FP64 value lies within a few FP64 ulps of an FP32 rounding boundary).
+                        Meant for MER_DETERMINISTIC backward passes, whose edge term reads the image; slower
+                        (GB300's FP64 rate is low). */
 } mer_shading;
 
 /* Terms computed by mer_backward (bit mask). */
@@ -101,10 +108,19 @@ enum {
     MER_EDGE = 1,      /* micro-edge term (Eq. 11, Sec. 4.3, Eq. 12) */
     MER_INTERIOR = 2,  /* interior term Omega through barycentrics/interpolation/texture */
     MER_INTERSECT = 4, /* scatter at geometry intersections (Eq. 12); off = the paper's ablation */
-    MER_EXACT_CROSSING = 8 /* option: an overhang pair's gradient goes to the two endpoints of the edge
+    MER_EXACT_CROSSING = 8, /* option: an overhang pair's gradient goes to the two endpoints of the edge
                               through which the segment between the pixel centres leaves the foreground
                               triangle, weighted by the crossing's position along it (pair axis only),
                               instead of the foreground fragment's barycentrics */
+    MER_DETERMINISTIC = 16 /* option: every per-pixel quantity is computed in FP64 from the FP32 inputs and
+                              each pixel's contribution to a gradient component is rounded once to a fixed-point
+                              number with 52 fractional bits (two 64-bit words: resolution 2^-52); the sums are
+                              exact integer sums, so the result does not depend on the order of the additions:
+                              bitwise identical from run to run, for any bin tile, grid or stored / recomputed
+                              barycentrics.  A contribution of magnitude >= 2^33 sets MER_EFIXED (it is
+                              dropped); sums must stay below 2^42 in magnitude.  Needs a workspace of
+                              mer_backward_workspace_size bytes (the fixed-point sums live there during the
+                              call) and ignores the cover image.  Slower than the default path (FP64). */
 };
 
 /* Bits of the optional cover image [n,H,W] uint8 that the rasterizers write beside the index image.  It
@@ -198,9 +214,16 @@ int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, 
               const int32_t* index, const float* attr, const float* tex, const float* bg_host,
               const mer_shading* shading_host, float* image, void* status_ws, void* stream);
 
+/* Bytes of workspace a backward pass needs: 256 (the status header) without MER_DETERMINISTIC; with it, plus
+ * 16 bytes per vertex-gradient component (vertex_rows * 3: n * V for mer_backward, totals.vrecs for
+ * mer_batch_backward) and per attribute-gradient component (attr_rows * attr_channels: V or
+ * totals.mesh_rows rows; attr_channels = the channels of grad_attr the pass writes, 0 without grad_attr),
+ * rounded up to 256 bytes. */
+size_t mer_backward_workspace_size(int64_t vertex_rows, int64_t attr_rows, int attr_channels, int terms);
+
 /* Backward pass.  image / grad_image [n,H,W,C] are the shaded image passed
  * through the edge-gradient step and dL/d(image).  terms = MER_EDGE |
- * MER_INTERIOR | MER_INTERSECT (any subset), optionally | MER_EXACT_CROSSING.
+ * MER_INTERIOR | MER_INTERSECT (any subset), optionally | MER_EXACT_CROSSING | MER_DETERMINISTIC.
  *   MER_EDGE: every pair (x,y)-(x+1,y), (x,y)-(x,y+1) with differing ids:
  *     Eq. 11 summed over channels; classification by the exact coverage test of
  *     each pixel centre against the other pixel's triangle (Sec. 4.3): none ->
@@ -219,11 +242,15 @@ int mer_shade(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, 
  * cover [n,H,W] uint8 or NULL: the cover image the rasterizer wrote with this index image.  With it,
  * pairs whose neighbour triangle cannot cover the pixel centre (see MER_COVER_*) are not classified;
  * the results are the same as without it.  A cover image that does not belong to `index` can drop
- * scattering pairs (no memory fault). */
+ * scattering pairs (no memory fault).
+ * workspace: NULL (no device status is recorded; not allowed with MER_DETERMINISTIC), or 256-byte aligned
+ * device memory of workspace_bytes >= mer_backward_workspace_size(n * V, V, attribute channels, terms)
+ * bytes whose first 256 bytes are a status header (a mer_rasterize workspace qualifies: the backward
+ * overwrites only what lies after the header, which the raster no longer needs). */
 int mer_backward(const mer_vertex* vpix, int V, const int32_t* tris, int T, int n, int H, int W,
                  const int32_t* index, const uint8_t* cover, const float* image, const float* grad_image,
                  const float* attr, const float* tex, const mer_shading* shading_host, int terms,
-                 double* grad_vpix, float* grad_attr, void* status_ws, void* stream);
+                 double* grad_vpix, float* grad_attr, void* workspace, size_t workspace_bytes, void* stream);
 
 /* EdgeGrad module backward alone (Supp. B): mer_backward with terms =
  * MER_EDGE | (intersections ? MER_INTERSECT : 0) for an image of C channels. */
@@ -239,7 +266,8 @@ int mer_interpolate_backward(const float* attr, int C_attr, const int32_t* tris,
                              float* grad_attr, double* grad_vpix, void* status_ws, void* stream);
 
 /* Vertex transform backward (Supp. B): grad_verts [V,3] (+=) = sum over views
- * of R^T J^T grad_vpix with J = d(x_s, y_s, zeta)/d(X_c, Y_c, Z_c). */
+ * of R^T J^T grad_vpix with J = d(x_s, y_s, zeta)/d(X_c, Y_c, Z_c), in FP64, the views summed in order
+ * (deterministic), rounded once to FP32. */
 int mer_project_backward(int V, const mer_camera* cams, int n, const mer_vertex* vpix, const double* grad_vpix,
                          float* grad_verts, void* stream);
 
@@ -273,6 +301,8 @@ typedef struct mer_item {
 typedef struct mer_batch_totals {
     int64_t vrecs, trecs, pixels, tiles, btiles;
     int n_items, tile;
+    int64_t mesh_rows;      /* 1 + the largest world-vertex row any item uses (rows of verts / attr) */
+    double max_tri_density; /* largest T / (H W) over the items with pixels */
 } mer_batch_totals;
 
 /* Host-only: fills the offsets of items[0..n) (host array) for bin tile `tile` (16, 32 or 64) and the
@@ -307,17 +337,25 @@ int mer_batch_render(const mer_vertex* vpix, const int32_t* tris, const mer_item
                      const float* tex, const float* bg_host, const mer_shading* shading_host, float* image,
                      int persistent_ctas, void* stream);
 /* cover: [pixels] uint8 or NULL, as for mer_backward (written by mer_batch_rasterize / mer_batch_render
- * with the same index image). */
+ * with the same index image).  workspace: required (its header holds the backward's work queue), at least
+ * mer_backward_workspace_size(totals.vrecs, totals.mesh_rows, attribute channels, terms) bytes; the
+ * mer_batch_rasterize workspace of the same step qualifies when it is that large (the backward overwrites
+ * only what lies after its header). */
 int mer_batch_backward(const mer_vertex* vpix, const int32_t* tris, const mer_item* items,
                        const mer_batch_totals* totals, const int32_t* index, const uint8_t* cover,
                        const float* image,
                        const float* grad_image, const float* attr, const float* tex,
                        const mer_shading* shading_host, int terms, double* grad_vpix, float* grad_attr,
-                       void* workspace, int persistent_ctas, void* stream);
-/* grad_verts [rows of all items' meshes, 3] (+=): items sharing a mesh add into the same rows. */
+                       void* workspace, size_t workspace_bytes, int persistent_ctas, void* stream);
+/* grad_verts [rows of all items' meshes, 3] (+=): items sharing a mesh add into the same rows.
+ * workspace NULL: FP32 products added with FP32 atomics (the order of the additions across items that share
+ * a mesh varies from run to run).  workspace non-NULL (256-byte aligned, at least
+ * mer_backward_workspace_size(totals.mesh_rows, 0, 0, MER_DETERMINISTIC) bytes, header first): FP64 products,
+ * each rounded once to 64-bit fixed point with 32 fractional bits and summed exactly, so the result is bitwise
+ * reproducible (the counterpart of MER_DETERMINISTIC; MER_EFIXED for a term of magnitude >= 2^33). */
 int mer_batch_project_backward(const mer_camera* cams, const mer_item* items, const mer_batch_totals* totals,
                                const mer_vertex* vpix, const double* grad_vpix, float* grad_verts,
-                               void* stream);
+                               void* workspace, size_t workspace_bytes, void* stream);
 
 /* Forward gradients (Sec. 5): out [n,H,W,C] = the derivative of the shaded image along one scene
  * parameter whose effect on the projected vertices is tangent [n,V,3] = d(x_s, y_s, zeta)/d theta (FP32).
@@ -379,7 +417,7 @@ int mer_precond_solve_info(const void* workspace, int* iters, double* rel_residu
 
 /* Synchronises `stream`, reads and clears the device status word of a
  * workspace (or of a status buffer of at least 256 bytes passed as status_ws to
- * the other calls).  Returns MER_OK, MER_EOVERFLOW or MER_ERANGE; *total_bins
+ * the other calls).  Returns MER_OK, MER_EOVERFLOW, MER_ERANGE or MER_EFIXED; *total_bins
  * (if not NULL) receives the number of bin entries the last mer_rasterize
  * needed, so an overflowing caller can size the workspace exactly. */
 int mer_sync_status(void* workspace, int64_t* total_bins, void* stream);

@@ -683,15 +683,16 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
  * an integer (or y reaches a clamp edge).  A pixel is flagged when x or y lies
  * within eps of such a point, eps being a bound of the FP32 rounding error of
  * the texel coordinate when it is formed as the exact x_0 = u_0 TW - 1/2 plus the
- * offset sum_i b_i (x_i - x_0):  eps = 32 ulp TW sum_i |b_i||u_i - u_0| + 4 ulp
- * (ulp = 2^-24).  Either one-sided derivative is correct at such pixels.
+ * offset sum_i b_i (x_i - x_0):  eps = 32 ulp TW sum_i |b_i||u_i - u_0| + 4 ulp,
+ * with ulp the unit roundoff of that evaluation: 2^-24 for FP32; for an FP64
+ * evaluation a deliberately generous 2^-40 (the FP64 error of the same steps is
+ * ~2^-50 relative).  Either one-sided derivative is correct at such pixels.
  * ------------------------------------------------------------------------ */
 static int near_boundary(double x, double eps) { double f = x - floor(x); return f <= eps || 1.0 - f <= eps; }
 
 int orc_texel_ambiguity(const double* scr, const int32_t* tris, const int32_t* index, int H, int W,
-                        const float* attr, const orc_shading* sh, uint8_t* flags /* [H,W] */)
+                        const float* attr, const orc_shading* sh, double ulp, uint8_t* flags /* [H,W] */)
 {
-    const double ulp = 1.0 / 16777216.0;
     for (int y = 0; y < H; ++y) {
         for (int x = 0; x < W; ++x) {
             size_t p = (size_t)y * W + x;

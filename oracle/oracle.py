@@ -81,7 +81,7 @@ def lib():
         L.orc_shade.argtypes = [P, P, P, P, i, i, P, P, P, ctypes.POINTER(OrcShading), P]
         L.orc_shade.restype = i
         L.orc_backward.argtypes = [P, P, P, i, P, P, i, i, P, P, P, P, ctypes.POINTER(OrcShading), i, P, P, P, P, P]
-        L.orc_texel_ambiguity.argtypes = [P, P, P, i, i, P, ctypes.POINTER(OrcShading), P]
+        L.orc_texel_ambiguity.argtypes = [P, P, P, i, i, P, ctypes.POINTER(OrcShading), ctypes.c_double, P]
         L.orc_texel_ambiguity.restype = i
         L.orc_backward.restype = i
         L.orc_project_backward.argtypes = [P, i, ctypes.POINTER(OrcCamera), P, P]
@@ -221,8 +221,12 @@ def backward(scr, snap, flags, tris, index, image, grad_image, attr, sh, tex=Non
     return gs, ga, dict(zip(names, counts.tolist()))
 
 
-def texel_ambiguity(scr, tris, index, attr, sh, tex):
-    """Pixels whose texel coordinate is within the FP32 error bound of a cell boundary ([H,W] bool)."""
+FP32_ULP, FP64_ULP = 2.0 ** -24, 2.0 ** -40
+
+
+def texel_ambiguity(scr, tris, index, attr, sh, tex, ulp: float = FP32_ULP):
+    """Pixels whose texel coordinate is within the error bound of a cell boundary ([H,W] bool): ``ulp`` is the
+    unit roundoff of the evaluation compared against (FP32_ULP, or FP64_ULP for FP64 arithmetic)."""
     H, W = index.shape
     out = np.zeros((H, W), np.uint8)
     if sh.uv_offset < 0 or tex is None:
@@ -231,7 +235,7 @@ def texel_ambiguity(scr, tris, index, attr, sh, tex):
     s = shading(sh, attr.shape[1], tex)
     lib().orc_texel_ambiguity(_p(scr), _p(np.ascontiguousarray(tris, dtype=np.int32)),
                               _p(np.ascontiguousarray(index, dtype=np.int32)), H, W, _p(attr), ctypes.byref(s),
-                              _p(out))
+                              float(ulp), _p(out))
     return out.astype(bool)
 
 
@@ -290,7 +294,7 @@ def project_backward(verts, cam, grad_scr):
 # ---------------------------------------------------------------------------
 
 class ViewResult:
-    __slots__ = ("scr", "snap", "flags", "index", "tie", "lam", "bary", "depth", "image", "texamb")
+    __slots__ = ("scr", "snap", "flags", "index", "tie", "lam", "bary", "depth", "image", "texamb", "texamb64")
 
 
 def render_view(verts, tris, cam, H, W, attr, sh, tex=None) -> ViewResult:
@@ -300,6 +304,7 @@ def render_view(verts, tris, cam, H, W, attr, sh, tex=None) -> ViewResult:
     r.lam, r.bary, r.depth = pixel_values(r.scr, tris, r.index)
     r.image = shade(r.scr, tris, r.index, attr, sh, tex, r.snap)
     r.texamb = texel_ambiguity(r.scr, tris, r.index, attr, sh, tex)
+    r.texamb64 = texel_ambiguity(r.scr, tris, r.index, attr, sh, tex, FP64_ULP)
     return r
 
 
@@ -315,14 +320,17 @@ def render(scene, views=None, threads: int | None = None) -> list[ViewResult]:
 
 
 def backward_scene(scene, results: list[ViewResult], grad_images, views=None,
-                   mode: int = EDGE | INTERIOR | INTERSECT, threads: int | None = None, want_attr=False):
-    """Per-view grad_scr list, summed world grad_verts [V,3], per-view counts (and grad_attr)."""
+                   mode: int = EDGE | INTERIOR | INTERSECT, threads: int | None = None, want_attr=False,
+                   images=None):
+    """Per-view grad_scr list, summed world grad_verts [V,3], per-view counts (and grad_attr).  ``images``: the
+    images passed through the edge step, one per view (default: each view's own rendered image)."""
     views = list(range(scene.n_views) if views is None else views)
 
     def one(k):
         i = views[k]
         r = results[k]
-        gs, ga, cnt, gabs = backward(r.scr, r.snap, r.flags, scene.tris, r.index, r.image, grad_images[k],
+        img = r.image if images is None else images[k]
+        gs, ga, cnt, gabs = backward(r.scr, r.snap, r.flags, scene.tris, r.index, img, grad_images[k],
                                      scene.attr, scene.shading, scene.tex, mode, want_attr, want_abs=True)
         gw = project_backward(scene.verts, scene.cams[i], gs)
         cnt["grad_abs"] = gabs

@@ -26,7 +26,7 @@ from .render import Renderer
 
 class BatchRenderer:
     def __init__(self, meshes, items, cams, shading, C_attr: int, tex=None, tile: int = 32, persistent_ctas: int = 0,
-                 device: str = "cuda", cover_hint: bool = True):
+                 device: str = "cuda", cover_hint: bool = True, precise: bool = False):
         """meshes: list of (verts [V,3] float32, tris [T,3] int32); items: list of (mesh, cam, H, W);
         cams: structured camera array; tex: texture tensor on the device or None.  cover_hint: the raster also
         writes the cover image and the backward skips the pixel pairs it shows cannot scatter (same results)."""
@@ -56,7 +56,7 @@ class BatchRenderer:
         self.items = torch.from_numpy(raw).to(device)
         self.item_pix = [(arr[k].pix, arr[k].H, arr[k].W) for k in range(len(items))]
         self.cams = B.cameras_tensor(cams, device)
-        self.sh = B.shading_struct(shading, C_attr, tex)
+        self.sh = B.shading_struct(shading, C_attr, tex, precise)
         self.bg = shading.bg_array()
         tot = self.tot
         self.vpix = torch.empty((max(tot.vrecs, 1), B.VERTEX_FLOATS), dtype=torch.float32, device=device)
@@ -68,9 +68,19 @@ class BatchRenderer:
         self._alloc_workspace(0)
         self.graph = None
 
-    def _alloc_workspace(self, capacity: int):
-        nbytes = B.mer_batch_workspace_size(self.tot, capacity)
+    def _alloc_workspace(self, capacity: int, at_least: int = 0):
+        nbytes = max(B.mer_batch_workspace_size(self.tot, capacity), at_least)
         self.workspace = torch.zeros((nbytes + 255) // 256 * 64, dtype=torch.float32, device=self.device)
+
+    def ensure_backward_workspace(self, terms: int, grad_attr=None):
+        """Grow the workspace to what a backward with these terms needs (MER_DETERMINISTIC keeps its fixed-point
+        sums there); call before capturing a graph."""
+        need = max(B.mer_backward_workspace_size(self.tot.vrecs, self.tot.mesh_rows,
+                                                 B.attr_grad_channels(self.sh, grad_attr), terms),
+                   B.mer_backward_workspace_size(self.tot.mesh_rows, 0, 0, terms))
+        if self.workspace.numel() * 4 < need:
+            self._alloc_workspace(0, need)
+            self.graph = None
 
     # -- stages ------------------------------------------------------------------------------------
     def forward(self, verts, attr, tex=None, depth=None, bary=None, fused: bool = True):
@@ -90,10 +100,13 @@ class BatchRenderer:
     def backward(self, grad_image, attr, tex=None, terms: int = 7, grad_attr=None):
         self.grad_vpix.zero_()
         self.grad_verts.zero_()
+        if terms & B.MER_DETERMINISTIC:
+            self.ensure_backward_workspace(terms, grad_attr)
         B.mer_batch_backward(self.vpix, self.tris, self.items, self.tot, self.index, self.image, grad_image, attr, tex,
                              self.sh, terms, self.grad_vpix, grad_attr, self.workspace, self.persistent_ctas,
                              self.cover)
-        B.mer_batch_project_backward(self.cams, self.items, self.tot, self.vpix, self.grad_vpix, self.grad_verts)
+        B.mer_batch_project_backward(self.cams, self.items, self.tot, self.vpix, self.grad_vpix, self.grad_verts,
+                                     self.workspace if terms & B.MER_DETERMINISTIC else None)
         return self.grad_verts
 
     def step(self, verts, attr, grad_image, tex=None, terms: int = 7):

@@ -15,8 +15,8 @@ import torch
 
 from . import build as _build
 
-MER_OK, MER_EINVAL, MER_ECUDA, MER_EOVERFLOW, MER_ERANGE = 0, 1, 2, 3, 4
-MER_EDGE, MER_INTERIOR, MER_INTERSECT, MER_EXACT_CROSSING = 1, 2, 4, 8
+MER_OK, MER_EINVAL, MER_ECUDA, MER_EOVERFLOW, MER_ERANGE, MER_EFIXED = 0, 1, 2, 3, 4, 5
+MER_EDGE, MER_INTERIOR, MER_INTERSECT, MER_EXACT_CROSSING, MER_DETERMINISTIC = 1, 2, 4, 8, 16
 CAMERA_DOUBLES = 17   # mer_camera: R[9], t[3], fx, fy, cx, cy, znear
 VERTEX_FLOATS = 8     # mer_vertex: 32 bytes
 
@@ -31,7 +31,7 @@ class MerShading(ctypes.Structure):
     _fields_ = [("n_main", ctypes.c_int), ("C", ctypes.c_int), ("uv_offset", ctypes.c_int),
                 ("mask_ch", ctypes.c_int), ("depth_ch", ctypes.c_int), ("C_attr", ctypes.c_int),
                 ("tex_h", ctypes.c_int), ("tex_w", ctypes.c_int), ("tex_c", ctypes.c_int),
-                ("backface_ch", ctypes.c_int)]
+                ("backface_ch", ctypes.c_int), ("precise", ctypes.c_int)]
 
 
 class MerItem(ctypes.Structure):
@@ -44,7 +44,7 @@ class MerItem(ctypes.Structure):
 class MerBatchTotals(ctypes.Structure):
     _fields_ = [("vrecs", ctypes.c_int64), ("trecs", ctypes.c_int64), ("pixels", ctypes.c_int64),
                 ("tiles", ctypes.c_int64), ("btiles", ctypes.c_int64), ("n_items", ctypes.c_int),
-                ("tile", ctypes.c_int)]
+                ("tile", ctypes.c_int), ("mesh_rows", ctypes.c_int64), ("max_tri_density", ctypes.c_double)]
 
 
 # (name, argtypes, restype); P = pointer, I = int, Z = size_t, L = int64
@@ -57,8 +57,9 @@ _SIGS = {
     "mer_project_screen": ([_P, _I, _I, _P, _P], _I),
     "mer_rasterize": ([_P, _I, _P, _I, _I, _I, _I, _I, _P, _Z, _P, _P, _P, _P, _P], _I),
     "mer_shade": ([_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(MerShading), _P, _P, _P], _I),
+    "mer_backward_workspace_size": ([_L, _L, _I, _I], _Z),
     "mer_backward": ([_P, _I, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, ctypes.POINTER(MerShading), _I, _P, _P,
-                      _P, _P], _I),
+                      _P, _Z, _P], _I),
     "mer_edge_grad_backward": ([_P, _P, _I, _P, _P, _I, _P, _I, _I, _I, _I, _I, _P, _P, _P], _I),
     "mer_interpolate_backward": ([_P, _I, _P, _I, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P, _P], _I),
     "mer_project_backward": ([_I, _P, _I, _P, _P, _P, _P], _I),
@@ -85,8 +86,8 @@ _SIGS = {
     "mer_batch_render": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _Z, _P, _P, _P, _P, _P, _P, _P,
                           ctypes.POINTER(MerShading), _P, _I, _P], _I),
     "mer_batch_backward": ([_P, _P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P, _P, _P,
-                            ctypes.POINTER(MerShading), _I, _P, _P, _P, _I, _P], _I),
-    "mer_batch_project_backward": ([_P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P], _I),
+                            ctypes.POINTER(MerShading), _I, _P, _P, _P, _Z, _I, _P], _I),
+    "mer_batch_project_backward": ([_P, _P, ctypes.POINTER(MerBatchTotals), _P, _P, _P, _P, _Z, _P], _I),
 }
 
 _lib = None
@@ -145,14 +146,26 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def shading_struct(sh, C_attr: int, tex: torch.Tensor | None) -> MerShading:
+def _nbytes(t: torch.Tensor | None) -> int:
+    return 0 if t is None else t.numel() * t.element_size()
+
+
+def shading_struct(sh, C_attr: int, tex: torch.Tensor | None, precise: bool = False) -> MerShading:
     s = MerShading()
     s.n_main, s.C, s.uv_offset, s.mask_ch, s.depth_ch = sh.n_main, sh.C, sh.uv_offset, sh.mask_ch, sh.depth_ch
     s.C_attr = C_attr
     s.tex_h, s.tex_w = (int(tex.shape[0]), int(tex.shape[1])) if tex is not None else (0, 0)
     s.tex_c = int(tex.shape[2]) if tex is not None else 0
     s.backface_ch = getattr(sh, "backface_ch", -1)
+    s.precise = int(bool(precise))
     return s
+
+
+def attr_grad_channels(sh: MerShading, grad_attr) -> int:
+    """Channels of grad_attr a backward pass writes (the interpolated ones, or u and v)."""
+    if grad_attr is None:
+        return 0
+    return sh.n_main if sh.uv_offset < 0 else 2
 
 
 def cameras_tensor(cams: np.ndarray, device="cuda") -> torch.Tensor:
@@ -196,13 +209,18 @@ def mer_shade(vpix, tris, index, attr, tex, bg: np.ndarray, sh: MerShading, imag
                            _stream()), "mer_shade")
 
 
+def mer_backward_workspace_size(vertex_rows: int, attr_rows: int, attr_channels: int, terms: int) -> int:
+    return int(lib().mer_backward_workspace_size(vertex_rows, attr_rows, attr_channels, terms))
+
+
 def mer_backward(vpix, tris, index, image, grad_image, attr, tex, sh: MerShading, terms: int, grad_vpix,
                  grad_attr=None, status_ws=None, cover=None):
+    """``status_ws``: the workspace (status header; with MER_DETERMINISTIC also the fixed-point sums)."""
     n, V = vpix.shape[0], vpix.shape[1]
     H, W = index.shape[1], index.shape[2]
     _check(lib().mer_backward(_ptr(vpix), V, _ptr(tris), tris.shape[0], n, H, W, _ptr(index), _ptr(cover), _ptr(image),
                               _ptr(grad_image), _ptr(attr), _ptr(tex), ctypes.byref(sh), terms, _ptr(grad_vpix),
-                              _ptr(grad_attr), _ptr(status_ws), _stream()), "mer_backward")
+                              _ptr(grad_attr), _ptr(status_ws), _nbytes(status_ws), _stream()), "mer_backward")
 
 
 def mer_edge_grad_backward(image, grad_image, index, vpix, tris, intersections: bool, grad_vpix, status_ws=None):
@@ -358,11 +376,14 @@ def mer_batch_backward(vpix, tris, items_dev, tot, index, image, grad_image, att
                        grad_vpix, grad_attr, workspace, persistent_ctas=0, cover=None):
     _check(lib().mer_batch_backward(_ptr(vpix), _ptr(tris), _ptr(items_dev), ctypes.byref(tot), _ptr(index),
                                     _ptr(cover), _ptr(image), _ptr(grad_image), _ptr(attr), _ptr(tex), ctypes.byref(sh), terms,
-                                    _ptr(grad_vpix), _ptr(grad_attr), _ptr(workspace), persistent_ctas, _stream()),
+                                    _ptr(grad_vpix), _ptr(grad_attr), _ptr(workspace), _nbytes(workspace),
+                                    persistent_ctas, _stream()),
            "mer_batch_backward")
 
 
-def mer_batch_project_backward(cams, items_dev, tot, vpix, grad_vpix, grad_verts):
+def mer_batch_project_backward(cams, items_dev, tot, vpix, grad_vpix, grad_verts, workspace=None):
+    """workspace: None for the FP32 atomic path; a workspace tensor for the reproducible FP64 path."""
     _check(lib().mer_batch_project_backward(_ptr(cams), _ptr(items_dev), ctypes.byref(tot), _ptr(vpix),
-                                            _ptr(grad_vpix), _ptr(grad_verts), _stream()),
+                                            _ptr(grad_vpix), _ptr(grad_verts), _ptr(workspace), _nbytes(workspace),
+                                            _stream()),
            "mer_batch_project_backward")

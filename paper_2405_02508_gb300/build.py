@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmer.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["abi.cu", "project.cu", "raster.cu", "shade.cu", "backward.cu", "solve.cu", "forward.cu", "normals.cu", "loss.cu"]
+UNITS = ["abi.cu", "project.cu", "raster.cu", "shade.cu", "backward.cu", "backward_det.cu", "solve.cu", "forward.cu", "normals.cu", "loss.cu"]
 HEADERS = ["mer_device.cuh", "shade_device.cuh"]
 
 

@@ -35,10 +35,14 @@ static_assert(kTW == 32 && kTH == kRows * kThreads / 32, "a warp spans the tile'
 // Per-tile triangle table of 2^BITS slots: a 32x16 tile of the head-scale workloads holds ~20-80 triangles.
 // 128 slots keep six CTAs resident with most of the SM's on-chip memory left to the L1 cache that serves the
 // vertex, texel and image gathers (256 slots measured 2.7 % slower on the multi-view head workload); a tile
-// with more triangles sends the excess straight to global memory, so launches whose meshes are dense on
-// screen (more than 0.1 triangle per pixel) take 256 slots.
+// with more triangles sends the excess straight to global memory, so launches in which some item is dense on
+// screen (more than 0.1 triangle per pixel) take 256 slots.  Only the variant without attribute gradients and
+// without the exact-crossing option has the 256-slot instantiation: launches with either always use 128.
 constexpr int kTableBits = 7, kTableBitsDense = 8;
 constexpr double kDenseTrianglesPerPixel = 0.1;
+// A triangle insert probes at most this many slots before it goes to global memory, so a tile with more
+// triangles than slots does not pay a scan of the whole table for every excess triangle.
+constexpr int kMaxProbes = 16;
 template <int NA, bool EXACT, int BITS>
 struct TriTable {
     static constexpr int kBits = BITS;
@@ -78,13 +82,14 @@ __device__ __forceinline__ void tri_normal(const VRec r[3], float N[3]) {
     N[2] = diff_of_products(e[0][0], e[1][1], e[0][1], e[1][0]);
 }
 
-// Slot of triangle `key` in the tile table of 2^BITS slots, inserting it if needed; -1 if the table is full.
+// Slot of triangle `key` in the tile table of 2^BITS slots, inserting it if needed; -1 if no slot was free
+// within kMaxProbes probes.
 template <int BITS>
 __device__ __forceinline__ int table_slot(int* keys, int key) {
     constexpr int kSlots = 1 << BITS;
     unsigned h = ((unsigned)key * 2654435761u) >> (32 - BITS);
 #pragma unroll 1
-    for (int probe = 0; probe < kSlots; ++probe) {
+    for (int probe = 0; probe < kMaxProbes && probe < kSlots; ++probe) {
         // a slot's key only ever changes from -1 to a triangle id within a tile: a key already seen is final
         int k = *reinterpret_cast<volatile int*>(keys + h);
         if (k == key) return (int)h;
@@ -718,11 +723,12 @@ int attr_channels(const mer_shading* sh, const float* grad_attr) {
 }
 }  // namespace
 
+// max_tri_density: the largest T / (H W) over the items (the table size follows the densest item).
 extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
                                          long long btiles, const int* index, const unsigned char* cover,
                                          const float* image, const float* grad_image, const float* attr, const float* tex,
                                          const mer_shading* sh, int terms, double* grad_vpix, float* grad_attr,
-                                         void* ws, int persistent_ctas, double tris_per_pixel, cudaStream_t s) {
+                                         void* ws, int persistent_ctas, double max_tri_density, cudaStream_t s) {
     if (btiles == 0) return 0;
     BwdArgs a;
     a.sh = *sh;
@@ -732,30 +738,44 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
     a.tex_vec4 = a.tex_stride == 4 && tex && (reinterpret_cast<uintptr_t>(tex) & 15u) == 0;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     if (cudaMemsetAsync(&hdr->queue_backward, 0, sizeof(unsigned long long), s) != cudaSuccess) return 2;
-    // persistent_ctas sizes the raster's grid (4 resident CTAs per SM); the backward keeps as many waves
-    unsigned grid = persistent_ctas > 0 ? (unsigned)((long long)persistent_ctas * kCtasPerSm / 4) : 0u;
-    if (grid == 0) {
-        int per_sm = 0, sms = 0, dev = 0;
+    // persistent_ctas sizes the raster's grid (4 resident CTAs per SM); the backward keeps as many waves.
+    // Without it, the grid is the device's SM count times the resident CTAs of the instantiation launched.
+    const unsigned fixed_grid = persistent_ctas > 0 ? (unsigned)((long long)persistent_ctas * kCtasPerSm / 4) : 0u;
+    unsigned grid = fixed_grid;
+    int sms = 0;
+    if (fixed_grid == 0) {
+        int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 2;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 2;
-        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_backward_batch<0, false, kTableBits>, kThreads, 0);
-        if (e != cudaSuccess) return 2;
-        grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
     }
     const bool exact = (terms & MER_EXACT_CROSSING) != 0;
+    // the resident-CTA grid of kernel k (when no grid was given)
+    auto grid_of = [&](const void* k) -> unsigned {
+        if (fixed_grid > 0) return fixed_grid;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0) != cudaSuccess) return 0u;
+        return (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
+    };
 #define MER_BWD_BATCH(A, E)                                                                                        \
-    k_backward_batch<A, E, kTableBits><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index, cover, image, grad_image, \
-                                                     attr, tex, a, grad_vpix, grad_attr, ws)
-    const bool dense = tris_per_pixel > kDenseTrianglesPerPixel;
+    do {                                                                                                           \
+        grid = grid_of((const void*)k_backward_batch<A, E, kTableBits>);                                           \
+        if (grid == 0) return 2;                                                                                   \
+        k_backward_batch<A, E, kTableBits><<<grid, kThreads, 0, s>>>(vpix, tris, items, n_items, btiles, index,   \
+                                                                     cover, image, grad_image, attr, tex, a,      \
+                                                                     grad_vpix, grad_attr, ws);                   \
+    } while (0)
+    const bool dense = max_tri_density > kDenseTrianglesPerPixel;
     switch (attr_channels(sh, grad_attr) * 2 + (exact ? 1 : 0)) {
         case 0:
-            if (dense)
+            if (dense) {
+                grid = grid_of((const void*)k_backward_batch<0, false, kTableBitsDense>);
+                if (grid == 0) return 2;
                 k_backward_batch<0, false, kTableBitsDense><<<grid, kThreads, 0, s>>>(
                     vpix, tris, items, n_items, btiles, index, cover, image, grad_image, attr, tex, a, grad_vpix,
                     grad_attr, ws);
-            else
+            } else {
                 MER_BWD_BATCH(0, false);
+            }
             break;
         case 1: MER_BWD_BATCH(0, true); break;
         case 2: MER_BWD_BATCH(1, false); break;

@@ -29,6 +29,7 @@ struct WsHeader {
 static_assert(sizeof(WsHeader) == 256, "header");
 constexpr int kStatusOverflow = 1;
 constexpr int kStatusRange = 2;
+constexpr int kStatusFixed = 4;  // a deterministic-mode contribution beyond the fixed-point range
 
 // Backward tile: 32 x 16 pixels, one CTA of 8 warps (two rows each); the batch plan counts items in these.
 constexpr int kBwdTileW = 32, kBwdTileH = 16;

@@ -3,7 +3,8 @@
 // Forward in FP64 with a fixed operation order and correctly rounded intrinsics
 // (no contraction into FMA), so the snapped screen positions X = rint(256 x_s)
 // are reproducible bit for bit by any IEEE FP64 implementation of the same
-// formula.  Backward in FP32.
+// formula.  Backward: the per-view kernel in FP64 (sums over the views in a fixed order); the batched one
+// in FP32 with atomics, or, given a workspace, in FP64 with fixed-point sums (bitwise reproducible).
 #include <cuda_runtime.h>
 
 #include "mer_device.cuh"
@@ -88,6 +89,24 @@ __device__ __forceinline__ bool world_grad(const mer_vertex& r, const mer_camera
     return true;
 }
 
+// world_grad in FP64 (vertex position from the exact snapped part plus the residual, zeta from its hi + lo
+// split).
+__device__ __forceinline__ bool world_grad_f64(const mer_vertex& r, const mer_camera& c, const double* g3,
+                                               double out[3]) {
+    if ((r.flags & 1u) == 0u) return false;
+    const double gx = g3[0], gy = g3[1], gz = g3[2];
+    const double z = (double)r.zeta + (double)r.zeta_lo;
+    const double xs = ((double)r.X * (1.0 / 256.0) - c.cx) + (double)r.rx;
+    const double ys = ((double)r.Y * (1.0 / 256.0) - c.cy) + (double)r.ry;
+    const double gX = gx * c.fx * z;
+    const double gY = gy * c.fy * z;
+    const double gZ = -z * (gx * xs + gy * ys + gz * z);
+    out[0] = c.R[0] * gX + c.R[3] * gY + c.R[6] * gZ;
+    out[1] = c.R[1] * gX + c.R[4] * gY + c.R[7] * gZ;
+    out[2] = c.R[2] * gX + c.R[5] * gY + c.R[8] * gZ;
+    return true;
+}
+
 // Batched: one thread per (item, vertex); items sharing a mesh add into the same rows.
 __global__ void k_project_backward_batch(const mer_camera* __restrict__ cams, const mer_item* __restrict__ items,
                                          int n_items, long long vrecs, const mer_vertex* __restrict__ vpix,
@@ -104,20 +123,56 @@ __global__ void k_project_backward_batch(const mer_camera* __restrict__ cams, co
     atomicAdd(o + 2, w[2]);
 }
 
-// One thread per vertex, looping over the views: grad_world = sum_views R^T J^T g.
+// Batched, reproducible: FP64 products rounded once to fixed point with 52 fractional bits, held as two
+// 64-bit words (hi = floor(w 2^20), lo = the remainder in units of 2^-52, in [0, 2^32]), and added with
+// integer atomics into acc [mesh rows, 3, 2] (exact, so the order does not matter); k_world_finalize converts.
+__global__ void k_project_backward_batch_fixed(const mer_camera* __restrict__ cams, const mer_item* __restrict__ items,
+                                               int n_items, long long vrecs, const mer_vertex* __restrict__ vpix,
+                                               const double* __restrict__ grad_vpix, unsigned long long* acc,
+                                               void* ws) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = block_find_item(items, n_items, (long long)blockIdx.x * blockDim.x, i, kFieldVrec);
+    if (i >= vrecs) return;
+    const mer_item m = items[k];
+    double w[3];
+    if (!world_grad_f64(vpix[i], cams[m.cam], grad_vpix + 3 * i, w)) return;
+    unsigned long long* o = acc + 6 * (size_t)(m.vert + (i - m.vrec));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (!(fabs(w[c]) < 8589934592.0)) {  // 2^33
+            set_status(ws, kStatusFixed);
+            continue;
+        }
+        const double h = floor(w[c] * 1048576.0);
+        const long long hi = (long long)h;
+        const long long lo = __double2ll_rn((w[c] - h * (1.0 / 1048576.0)) * 4503599627370496.0);
+        if (hi != 0) atomicAdd(o + 2 * c, (unsigned long long)hi);
+        if (lo != 0) atomicAdd(o + 2 * c + 1, (unsigned long long)lo);
+    }
+}
+
+__global__ void k_world_finalize(const unsigned long long* __restrict__ acc, long long n, float* __restrict__ grad_verts) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long lo = (long long)acc[2 * i + 1];
+    const long long hi = (long long)acc[2 * i] + (lo >> 32);
+    grad_verts[i] += __double2float_rn((double)hi * (1.0 / 1048576.0) + (double)(lo & 0xffffffffll) * (1.0 / 4503599627370496.0));
+}
+
+// One thread per vertex, looping over the views: grad_world = sum_views R^T J^T g (FP64).
 __global__ void k_project_backward(int V, const mer_camera* __restrict__ cams, int n,
                                    const mer_vertex* __restrict__ vpix, const double* __restrict__ grad_vpix,
                                    float* __restrict__ grad_verts) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;  // sum over views in FP64, products in FP32
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     for (int view = 0; view < n; ++view) {
         const size_t k = (size_t)view * V + v;
-        float w[3];
-        if (!world_grad(vpix[k], cams[view], grad_vpix + 3 * k, w)) continue;
-        a0 += (double)w[0];
-        a1 += (double)w[1];
-        a2 += (double)w[2];
+        double w[3];
+        if (!world_grad_f64(vpix[k], cams[view], grad_vpix + 3 * k, w)) continue;
+        a0 += w[0];
+        a1 += w[1];
+        a2 += w[2];
     }
     grad_verts[3 * (size_t)v] += (float)a0;
     grad_verts[3 * (size_t)v + 1] += (float)a1;
@@ -157,10 +212,22 @@ extern "C" int mer_launch_project_batch(const float* verts, const mer_camera* ca
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 
+// ws: null for the FP32 atomic path; else a workspace whose bytes after the 256-byte header hold
+// mesh_rows * 3 two-word fixed-point sums (the reproducible FP64 path).
 extern "C" int mer_launch_project_backward_batch(const mer_camera* cams, const mer_item* items, int n_items,
-                                                 long long vrecs, const mer_vertex* vpix, const double* grad_vpix,
-                                                 float* grad_verts, cudaStream_t s) {
+                                                 long long vrecs, long long mesh_rows, const mer_vertex* vpix,
+                                                 const double* grad_vpix, float* grad_verts, void* ws,
+                                                 cudaStream_t s) {
     if (vrecs == 0) return 0;
+    if (ws) {
+        unsigned long long* acc = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws) + 256);
+        if (cudaMemsetAsync(acc, 0, (size_t)mesh_rows * 48, s) != cudaSuccess) return 2;
+        k_project_backward_batch_fixed<<<(unsigned)((vrecs + 255) / 256), 256, 0, s>>>(cams, items, n_items, vrecs,
+                                                                                       vpix, grad_vpix, acc, ws);
+        const long long n = 3 * mesh_rows;
+        if (n > 0) k_world_finalize<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, n, grad_verts);
+        return cudaGetLastError() == cudaSuccess ? 0 : 2;
+    }
     k_project_backward_batch<<<(unsigned)((vrecs + 255) / 256), 256, 0, s>>>(cams, items, n_items, vrecs, vpix,
                                                                              grad_vpix, grad_verts);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;

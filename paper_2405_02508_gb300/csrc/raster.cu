@@ -715,11 +715,23 @@ extern "C" int mer_launch_batch_rasterize(const mer_vertex* vpix, const int* tri
                         persistent_ctas, s);
 }
 
+extern "C" int mer_launch_shade_batch(const mer_vertex*, const int*, const mer_item*, int, long long, const int*,
+                                      const float*, const float*, const float*, const mer_shading*, float*, void*,
+                                      cudaStream_t);
+
 extern "C" int mer_launch_batch_render(const mer_vertex* vpix, const int* tris, const mer_item* items, int n_items,
-                                       long long trecs, long long tiles, int tile, void* ws, size_t ws_bytes,
-                                       int* index, float* depth, float* bary, unsigned char* cover, const float* attr,
-                                       const float* tex, const float* bg, const mer_shading* sh, float* image,
-                                       int persistent_ctas, cudaStream_t s) {
+                                       long long trecs, long long tiles, long long pixels, int tile, void* ws,
+                                       size_t ws_bytes, int* index, float* depth, float* bary, unsigned char* cover,
+                                       const float* attr, const float* tex, const float* bg, const mer_shading* sh,
+                                       float* image, int persistent_ctas, cudaStream_t s) {
+    if (sh->precise) {
+        // FP64 shading: the raster pass alone, then the precise shading pass over the index image (the
+        // results the fused pass would give with FP64 shading)
+        const int rc = batch_raster(vpix, tris, items, n_items, trecs, tiles, tile, ws, ws_bytes, index, depth, bary,
+                                    cover, nullptr, persistent_ctas, s);
+        if (rc) return rc;
+        return mer_launch_shade_batch(vpix, tris, items, n_items, pixels, index, attr, tex, bg, sh, image, ws, s);
+    }
     ShadeOut so;
     so.a = make_shade_args(tex, bg, sh);
     so.attr = attr;

@@ -11,7 +11,9 @@ centre, one byte a pixel) and the backward uses it to skip pixel pairs that cann
 the same without it.
 
 ``MerRender.apply(verts, attr, tex, cams, renderer, recompute_bary)`` exposes the
-same as an autograd function whose backward is the micro-edge kernel.  With
+same as an autograd function whose backward is the micro-edge kernel (with the
+renderer's ``terms``; with MER_DETERMINISTIC among them the gradients are bitwise
+reproducible).  With
 ``recompute_bary`` the barycentric image is never stored (the backward always
 re-derives barycentrics from the index image and the vertex records), which
 saves 8 bytes per pixel of activation memory.
@@ -26,7 +28,10 @@ from . import binding as B
 
 class Renderer:
     def __init__(self, tris: torch.Tensor, V: int, n_views: int, H: int, W: int, shading, C_attr: int,
-                 tex_shape=None, tile: int = 16, device: str = "cuda", cover_hint: bool = True):
+                 tex_shape=None, tile: int = 16, device: str = "cuda", cover_hint: bool = True,
+                 precise: bool = False):
+        """precise: FP64 shading rounded once per value (the image a MER_DETERMINISTIC backward expects).
+        ``terms`` (attribute): the backward terms MerRender uses."""
         self.tris = tris.to(device=device, dtype=torch.int32).contiguous()
         self.T = int(self.tris.shape[0])
         self.V, self.n, self.H, self.W = int(V), int(n_views), int(H), int(W)
@@ -34,7 +39,7 @@ class Renderer:
         self.device = device
         self.shading = shading
         self.C = shading.C
-        self.sh = B.shading_struct(shading, C_attr, None)
+        self.sh = B.shading_struct(shading, C_attr, None, precise)
         if tex_shape is not None:
             self.sh.tex_h, self.sh.tex_w = int(tex_shape[0]), int(tex_shape[1])
             self.sh.tex_c = int(tex_shape[2]) if len(tex_shape) > 2 else shading.n_main
@@ -46,11 +51,17 @@ class Renderer:
         self.cover = torch.empty((n, H, W), dtype=torch.uint8, device=device) if cover_hint else None
         self.grad_vpix = torch.zeros((n, self.V, 3), dtype=torch.float64, device=device)
         self.grad_verts = torch.zeros((self.V, 3), dtype=torch.float32, device=device)
+        self.terms = B.MER_EDGE | B.MER_INTERIOR | B.MER_INTERSECT
         self._alloc_workspace(0)
 
-    def _alloc_workspace(self, capacity: int):
-        nbytes = B.mer_workspace_size(self.V, self.T, self.n, self.H, self.W, self.tile, capacity)
+    def _alloc_workspace(self, capacity: int, at_least: int = 0):
+        nbytes = max(B.mer_workspace_size(self.V, self.T, self.n, self.H, self.W, self.tile, capacity), at_least)
         self.workspace = torch.zeros((nbytes + 255) // 256 * 64, dtype=torch.float32, device=self.device)
+
+    def _ensure_backward_workspace(self, terms: int, grad_attr):
+        need = B.mer_backward_workspace_size(self.n * self.V, self.V, B.attr_grad_channels(self.sh, grad_attr), terms)
+        if self.workspace.numel() * 4 < need:  # the raster's bins are not needed any more at this point
+            self._alloc_workspace(0, need)
 
     # -- forward -----------------------------------------------------------------------------------
     def project(self, verts: torch.Tensor, cams: torch.Tensor):
@@ -88,6 +99,7 @@ class Renderer:
         if zero:
             self.grad_vpix.zero_()
             self.grad_verts.zero_()
+        self._ensure_backward_workspace(terms, grad_attr)
         B.mer_backward(self.vpix, self.tris, self.index, self.image, grad_image.contiguous(), attr.contiguous(), tex,
                        self.sh, terms, self.grad_vpix, grad_attr, self.workspace, self.cover)
         B.mer_project_backward(cams, self.vpix, self.grad_vpix, self.grad_verts)
@@ -141,5 +153,5 @@ class MerRender(torch.autograd.Function):
         r.index.copy_(index)
         r.image.copy_(image)
         grad_attr = torch.zeros_like(attr) if ctx.needs_input_grad[1] else None
-        gv = r.backward(grad_image, cams, attr, tex, grad_attr=grad_attr)
+        gv = r.backward(grad_image, cams, attr, tex, terms=r.terms, grad_attr=grad_attr)
         return gv.clone(), grad_attr, None, None, None, None

@@ -69,8 +69,22 @@ def test_batch_plan_offsets():
     assert [arr[k].btile for k in range(3)] == [0, 6, 6]  # backward tiles of 32 x 16: ceil(50/32) * ceil(40/16)
     assert (tot.vrecs, tot.trecs, tot.pixels, tot.tiles, tot.btiles) == (15, 10, 2000 + 561, 4 + 2, 6 + 4)
     assert binding.mer_batch_workspace_size(tot) > 0
+    assert tot.mesh_rows == 10  # every item starts at world row 0 here: the largest V
+    assert tot.max_tri_density == max(7 / 2000, 3 / 561)
     arr[0].H = 9000
     import pytest
 
     with pytest.raises(binding.MerError):
         binding.mer_batch_plan(arr, 32)
+
+
+def test_backward_workspace_sizes():
+    """Host-only sizing of the backward workspace: the status header alone, or with MER_DETERMINISTIC the
+    fixed-point sums of the vertex and attribute gradients (each part rounded up to 256 bytes)."""
+    from paper_2405_02508_gb300 import binding as B
+
+    assert B.mer_backward_workspace_size(1000, 500, 2, 7) == 256
+    det = 7 | B.MER_DETERMINISTIC
+    assert B.mer_backward_workspace_size(1000, 500, 2, det) == 256 + 48128 + 16128
+    assert B.mer_backward_workspace_size(10, 0, 0, det) == 256 + 512
+    assert B.mer_backward_workspace_size(-1, 0, 0, det) == 0

@@ -41,26 +41,41 @@ def _cuda():
     binding.lib()
 
 
+DET = 16  # MER_DETERMINISTIC
+
+
 def run_parity(orc, scene, grads, views=None, terms=ALL, tile=16, check_world=True, want_attr=False,
-               store_bary=True, cover_hint=True):
+               store_bary=True, cover_hint=True, label=None, tie_check=True):
+    """The scene through the CUDA path and the oracle, every compared view element by element (and the world
+    and attribute gradients when every view is compared).  With DET in ``terms``: FP64 shading and the
+    deterministic backward on the GPU, the oracle's image rounded to FP32 as its edge-step input, and the
+    stated gradient bound with no conditioning term."""
+    det = bool(terms & DET)
     gpu = parity.gpu_run(scene, grads, terms=terms, tile=tile, want_attr=want_attr, store_bary=store_bary,
                          cover_hint=cover_hint)
     views = list(range(scene.n_views)) if views is None else list(views)
     ovs = orc.render(scene, views)
-    gs, gw, counts, ga = orc.backward_scene(scene, ovs, [grads[v] for v in views], views, mode=terms,
-                                            want_attr=want_attr)
+    gs, gw, counts, ga = orc.backward_scene(scene, ovs, [grads[v] for v in views], views, mode=terms & 15,
+                                            want_attr=want_attr,
+                                            images=[parity.oracle_image(ov, det) for ov in ovs])
+    label = label or scene.name
     stats = []
     for k, v in enumerate(views):
-        stats.append(parity.compare_view(gpu, v, ovs[k], gs[k], scene.tris, S=counts[k]["grad_abs"]))
-    ex = np.unique(np.concatenate([parity.excluded_vertices(scene.tris, gpu.index[v], ovs[k].index, ovs[k].texamb)
+        stats.append(parity.compare_view(gpu, v, ovs[k], gs[k], scene.tris, S=counts[k]["grad_abs"],
+                                         deterministic=det, label=label))
+    if tie_check:
+        parity.assert_tie_share(stats)
+    ex = np.unique(np.concatenate([parity.excluded_vertices(scene.tris, gpu.index[v], ovs[k].index,
+                                                            parity.ambiguous(ovs[k], det))
                                    for k, v in enumerate(views)]))
+    cond = 0.0 if det else parity.GRAD_COND
     if check_world and len(views) == scene.n_views:
         Sw = parity.world_condition(scene, views, ovs, [c["grad_abs"] for c in counts])
-        nbad, worst = parity.grad_violations(gpu.grad_verts, gw, Sw, ex)
+        nbad, worst = parity.grad_violations(gpu.grad_verts, gw, Sw, ex, cond)
         assert nbad == 0, f"world gradients: {nbad} components outside tolerance (worst {worst:.3g})"
     if want_attr:
         Sa = sum(c["grad_attr_abs"] for c in counts)
-        nbad, worst = parity.grad_violations(gpu.grad_attr, ga, Sa, ex)
+        nbad, worst = parity.grad_violations(gpu.grad_attr, ga, Sa, ex, cond)
         assert nbad == 0, f"attribute gradients: {nbad} outside tolerance (worst {worst:.3g})"
     return gpu, stats, counts
 
@@ -165,13 +180,15 @@ def test_parity_multiview_full_size_sampled_views(orc):
 
 
 def test_parity_uneven_items(orc):
-    """Items of the uneven batch: smallest, largest and two in between."""
+    """Items of the uneven batch: smallest, largest and two in between (the flagged-tie share over the four)."""
     items = scenes.uneven_batch(n_items=256)
     T = np.array([len(it.tris) for it in items])
     order = np.argsort(T)
+    stats = []
     for i in [order[0], order[len(order) // 3], order[2 * len(order) // 3], order[-1]]:
         it = items[i]
-        run_parity(orc, it, it.upstream())
+        stats += run_parity(orc, it, it.upstream(), label=f"c5 item {i}", tie_check=False)[1]
+    parity.assert_tie_share(stats)
 
 
 # ---------------------------------------------------------------------------
