@@ -130,9 +130,10 @@ enum {
  * t_q's facing covers p, the pair's classification is known without loading either triangle.  This is an
  * implementation aid of this library; the paper has no counterpart and the results do not change.
  * Facing: "front" = negative snapped area (y down: counter-clockwise on screen), "back" = positive.
- * The counts leave out back-facing triangles that lie behind the whole bin tile (the raster skips them);
- * such a triangle wins no pixel of that tile, so the counts are exact for pairs inside one bin tile, and a
- * pair from a pixel across the border of its bin tile is always classified in full (the border bits). */
+ * The counts of front-facing triangles are exact.  Those of back-facing ones leave out back-facing triangles
+ * that lie behind the whole bin tile (the raster skips them); such a triangle wins no pixel of that tile, so
+ * the counts are exact for pairs inside one bin tile, and a pair from a pixel across the border of its bin
+ * tile whose neighbour's triangle is back-facing is always classified in full (the border bits). */
 enum {
     MER_COVER_SAME_2 = 1,       /* another triangle with the visible triangle's facing covers the centre */
     MER_COVER_OTHER_1 = 2,      /* a triangle with the other facing covers the centre */

@@ -160,15 +160,17 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
             bool pair = t >= 0 && tq != t && tq != -2;
             if (hinted && tq >= 0) {
                 // p's fragment can scatter only if q's triangle covers p's centre too (Sec. 4.3), which needs
-                // another triangle of q's facing at p (a second one when p's own triangle has that facing);
-                // a pair across the border of p's bin tile is always classified
+                // another triangle of q's facing at p (a second one when p's own triangle has that facing).
+                // The counts of front-facing triangles are exact everywhere; those of back-facing ones only for
+                // triangles that win a pixel of p's bin tile, so a pair across the border of p's bin tile whose
+                // neighbour triangle is back-facing is always classified.
                 const unsigned hq = S.scov[row + 1 + ddy][lane + 1 + ddx];
                 const bool same = ((hp ^ hq) & MER_COVER_WINNER_BACK) == 0;
                 const unsigned need = same ? MER_COVER_SAME_2 : MER_COVER_OTHER_1;
                 const unsigned border = d == 0 ? MER_COVER_BORDER_L
                                                 : (d == 1 ? MER_COVER_BORDER_R
                                                           : (d == 2 ? MER_COVER_BORDER_T : MER_COVER_BORDER_B));
-                pair = pair && (hp & (need | border)) != 0;
+                pair = pair && ((hp & need) != 0 || ((hp & border) != 0 && (hq & MER_COVER_WINNER_BACK) != 0));
             }
             m[4 * k + d] = __ballot_sync(full, pair);
             np[4 * k + d + 1] = np[4 * k + d] + __popc(m[4 * k + d]);
@@ -213,17 +215,19 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
         const int px = x0 + src, y = y0 + row;
         const int ts = S.sidx[row + 1][src + 1];
         const int tq = S.sidx[row + 1 + ddy][src + 1 + ddx];
-        int vs[3];
-        if (ts >= it.T || !tri_ids(it.tris, ts, it.V, vs)) {
-            set_status(ws, kStatusRange);
-            continue;
-        }
-        int Xs[3], Ys[3];
+        int vs[3] = {0, 0, 0};
+        int Xs[3] = {0, 0, 0}, Ys[3] = {0, 0, 0};
+        if (tq >= 0 || EXACT) {  // a pair against the background needs only Eq. 11 (the row pass checks ts)
+            if (ts >= it.T || !tri_ids(it.tris, ts, it.V, vs)) {
+                set_status(ws, kStatusRange);
+                continue;
+            }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vs[k]));
-            Xs[k] = xy.x;
-            Ys[k] = xy.y;
+            for (int k = 0; k < 3; ++k) {
+                const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vs[k]));
+                Xs[k] = xy.x;
+                Ys[k] = xy.y;
+            }
         }
         const int qx = px + ddx, qy = y + ddy;
         const int axis = ddx != 0 ? 0 : 1;
@@ -406,7 +410,7 @@ __device__ __forceinline__ void row_pass(const BItem& it, int tx, int ty, int ro
         if (a.terms & MER_INTERIOR) {
             const float z[3] = {rv[0].zeta, rv[1].zeta, rv[2].zeta};
             const float s = B.lam[0] * z[0] + B.lam[1] * z[1] + B.lam[2] * z[2];
-            const float is = 1.0f / s;
+            const float is = __frcp_rn(s);  // the correctly rounded 1 / s, as the division
             float b[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) b[k] = B.lam[k] * z[k] * is;

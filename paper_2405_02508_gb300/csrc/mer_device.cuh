@@ -285,18 +285,51 @@ struct Bary {
 __device__ __forceinline__ Bary screen_bary(const VRec v[3], int x, int y) {
     const int pxf = 256 * x + 128, pyf = 256 * y + 128;
     int ix[3], iy[3];
-    float a[3], b[3], r[3], s[3];
+    float r[3], s[3];
+    unsigned span = 0u;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         ix[i] = v[i].X - pxf;
         iy[i] = v[i].Y - pyf;
-        a[i] = i2f_exact(ix[i]) * (1.0f / 256.0f);
-        b[i] = i2f_exact(iy[i]) * (1.0f / 256.0f);
         r[i] = v[i].rx;
         s[i] = v[i].ry;
+        span |= (unsigned)(ix[i] + 32768) | (unsigned)(iy[i] + 32768);
     }
     Bary B;
-    float e[3];
+    float e[3], a[3], b[3];
+    if ((span >> 16) == 0u) {
+        // Every vertex within 128 px of the centre (the common case): |ix|, |iy| < 2^15, so the integer edge
+        // functions fit 32 bits, the coordinates convert exactly through the 1.5 * 2^23 bias, and differences
+        // of the converted coordinates are exact.  The same values as the general path below.
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            a[i] = (__int_as_float(0x4B400000 + ix[i]) - 12582912.0f) * (1.0f / 256.0f);
+            b[i] = (__int_as_float(0x4B400000 + iy[i]) - 12582912.0f) * (1.0f / 256.0f);
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int j = (i + 1) % 3, k = (i + 2) % 3;
+            const int E = ix[j] * iy[k] - iy[j] * ix[k];
+            const float lin = (a[j] * s[k] - s[j] * a[k]) + (r[j] * b[k] - b[j] * r[k]);
+            const float quad = r[j] * s[k] - s[j] * r[k];
+            e[i] = __fmaf_rn(__int2float_rn(E), 1.0f / 65536.0f, lin + quad);
+        }
+        B.d = (e[0] + e[1]) + e[2];
+        const float inv = __frcp_rn(B.d);  // the correctly rounded 1 / d, as the division
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int j = (i + 1) % 3, k = (i + 2) % 3;
+            B.lam[i] = e[i] * inv;
+            B.gx[i] = ((b[j] - b[k]) + (s[j] - s[k])) * inv;
+            B.gy[i] = ((a[k] - a[j]) + (r[k] - r[j])) * inv;
+        }
+        return B;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        a[i] = i2f_exact(ix[i]) * (1.0f / 256.0f);
+        b[i] = i2f_exact(iy[i]) * (1.0f / 256.0f);
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const int j = (i + 1) % 3, k = (i + 2) % 3;
@@ -306,7 +339,7 @@ __device__ __forceinline__ Bary screen_bary(const VRec v[3], int x, int y) {
         e[i] = __fmaf_rn(signed_ll2f_rn(E), 1.0f / 65536.0f, lin + quad);
     }
     B.d = (e[0] + e[1]) + e[2];
-    const float inv = 1.0f / B.d;
+    const float inv = __frcp_rn(B.d);  // the correctly rounded 1 / d, as the division
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const int j = (i + 1) % 3, k = (i + 2) % 3;

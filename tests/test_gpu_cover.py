@@ -29,10 +29,11 @@ def orc():
 
 
 def _may_scatter(cp, cq, border_bit):
-    """The backward's test for a pair whose neighbour q is covered: can q's triangle cover p's centre?"""
+    """The backward's test for a pair whose neighbour q is covered: can q's triangle cover p's centre?  (Across
+    the border of p's bin tile the back-facing counts may leave out q's triangle when it is back-facing.)"""
     same = ((cp ^ cq) & WINNER_BACK) == 0
     need = np.where(same, cp & SAME_2, cp & OTHER_1) != 0
-    return need | ((cp & border_bit) != 0)
+    return need | (((cp & border_bit) != 0) & ((cq & WINNER_BACK) != 0))
 
 
 def check_cover(orc, index, cover, snap, flags, tris, tile):
