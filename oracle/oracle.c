@@ -409,14 +409,18 @@ static void shade_pixel_dual(const double* scr, const int64_t* snap, const int32
 /* ------------------------------------------------------------------------
  * Interpolation module + deferred shading (Supp. B): shaded image [H,W,C].
  * ------------------------------------------------------------------------ */
-int orc_shade(const double* scr, const int64_t* snap, const int32_t* tris, const int32_t* index, int H, int W,
-              const float* attr, const float* tex, const float* bg, const orc_shading* sh,
-              double* image /* [H,W,C] */)
+/* Rows [y0, y1) only (the other rows of `image` are left as they are); orc_shade is all rows.  A view's
+ * rows are independent, so callers may shade bands of rows on separate threads. */
+int orc_shade_rows(const double* scr, const int64_t* snap, const int32_t* tris, const int32_t* index, int H, int W,
+                   const float* attr, const float* tex, const float* bg, const orc_shading* sh,
+                   double* image /* [H,W,C] */, int y0, int y1)
 {
     dual I[64];
     if (sh->C > 64) return -1;
     if (sh->backface_ch >= 0 && !snap) return -1;
-    for (int y = 0; y < H; ++y) {
+    if (y0 < 0) y0 = 0;
+    if (y1 > H) y1 = H;
+    for (int y = y0; y < y1; ++y) {
         for (int x = 0; x < W; ++x) {
             size_t p = (size_t)y * W + x;
             int t = index[p];
@@ -429,6 +433,13 @@ int orc_shade(const double* scr, const int64_t* snap, const int32_t* tris, const
         }
     }
     return 0;
+}
+
+int orc_shade(const double* scr, const int64_t* snap, const int32_t* tris, const int32_t* index, int H, int W,
+              const float* attr, const float* tex, const float* bg, const orc_shading* sh,
+              double* image /* [H,W,C] */)
+{
+    return orc_shade_rows(scr, snap, tris, index, H, W, attr, tex, bg, sh, image, 0, H);
 }
 
 /* ------------------------------------------------------------------------
@@ -511,13 +522,17 @@ static void gather(const double* scr, const int32_t* tris, int t, int x, int y, 
         }
 }
 
-int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, int V,
-                 const int32_t* tris, const int32_t* index, int H, int W,
-                 const double* image /* [H,W,C] */, const float* grad_image /* [H,W,C] */,
-                 const float* attr, const float* tex, const orc_shading* sh, int mode,
-                 double* grad_scr /* [V,3], accumulated */, double* grad_attr /* [V,C_attr] or NULL */,
-                 int64_t* counts /* [6] */, double* grad_abs /* [V,3] or NULL */,
-                 double* grad_attr_abs /* [V,C_attr] or NULL */)
+/* The part of orc_backward that belongs to rows [y0, y1): the interior term of those rows' pixels, the
+ * horizontal pairs in those rows and the vertical pairs (y, y + 1) with y in them.  The sum over a partition
+ * of the rows is orc_backward (up to the order of the FP64 additions); callers may run bands of rows on
+ * separate threads, each into its own accumulators. */
+int orc_backward_rows(const double* scr, const int64_t* snap, const int32_t* flags, int V,
+                      const int32_t* tris, const int32_t* index, int H, int W,
+                      const double* image /* [H,W,C] */, const float* grad_image /* [H,W,C] */,
+                      const float* attr, const float* tex, const orc_shading* sh, int mode,
+                      double* grad_scr /* [V,3], accumulated */, double* grad_attr /* [V,C_attr] or NULL */,
+                      int64_t* counts /* [6] */, double* grad_abs /* [V,3] or NULL */,
+                      double* grad_attr_abs /* [V,C_attr] or NULL */, int y0, int y1)
 {
     const int C = sh->C;
     dual I[64];
@@ -527,7 +542,7 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
         /* Omega: derivative of the shaded value of each covered pixel with the
          * index image held fixed (Eq. 5, second term), through the barycentrics
          * and interpolation (and texture) modules. */
-        for (int y = 0; y < H; ++y) {
+        for (int y = y0 < 0 ? 0 : y0; y < (y1 > H ? H : y1); ++y) {
             for (int x = 0; x < W; ++x) {
                 size_t p = (size_t)y * W + x;
                 int t = index[p];
@@ -591,7 +606,7 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
      * (x,y)-(x,y+1) inside the image (no pairs across the border). */
     for (int axis = 0; axis < 2; ++axis) {
         int dx = axis == 0 ? 1 : 0, dy = axis == 0 ? 0 : 1;
-        for (int y = 0; y + dy < H; ++y) {
+        for (int y = y0 < 0 ? 0 : y0; y < (y1 > H ? H : y1) && y + dy < H; ++y) {
             for (int x = 0; x + dx < W; ++x) {
                 int xa = x, ya = y, xb = x + dx, yb = y + dy;
                 size_t pa = (size_t)ya * W + xa, pb = (size_t)yb * W + xb;
@@ -675,6 +690,16 @@ int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, i
         }
     }
     return 0;
+}
+
+int orc_backward(const double* scr, const int64_t* snap, const int32_t* flags, int V,
+                 const int32_t* tris, const int32_t* index, int H, int W,
+                 const double* image, const float* grad_image, const float* attr, const float* tex,
+                 const orc_shading* sh, int mode, double* grad_scr, double* grad_attr, int64_t* counts,
+                 double* grad_abs, double* grad_attr_abs)
+{
+    return orc_backward_rows(scr, snap, flags, V, tris, index, H, W, image, grad_image, attr, tex, sh, mode,
+                             grad_scr, grad_attr, counts, grad_abs, grad_attr_abs, 0, H);
 }
 
 /* ------------------------------------------------------------------------

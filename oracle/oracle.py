@@ -80,7 +80,12 @@ def lib():
         L.orc_pixel_values.restype = i
         L.orc_shade.argtypes = [P, P, P, P, i, i, P, P, P, ctypes.POINTER(OrcShading), P]
         L.orc_shade.restype = i
+        L.orc_shade_rows.argtypes = [P, P, P, P, i, i, P, P, P, ctypes.POINTER(OrcShading), P, i, i]
+        L.orc_shade_rows.restype = i
         L.orc_backward.argtypes = [P, P, P, i, P, P, i, i, P, P, P, P, ctypes.POINTER(OrcShading), i, P, P, P, P, P]
+        L.orc_backward_rows.argtypes = [P, P, P, i, P, P, i, i, P, P, P, P, ctypes.POINTER(OrcShading), i, P, P, P,
+                                        P, P, i, i]
+        L.orc_backward_rows.restype = i
         L.orc_texel_ambiguity.argtypes = [P, P, P, i, i, P, ctypes.POINTER(OrcShading), ctypes.c_double, P]
         L.orc_texel_ambiguity.restype = i
         L.orc_backward.restype = i
@@ -176,43 +181,84 @@ def pixel_values(scr, tris, index):
     return lam, bary, depth
 
 
-def shade(scr, tris, index, attr, sh, tex=None, snap=None):
-    """Shaded image [H,W,C] f64; ``snap`` (snapped coordinates) is needed for a back-face channel."""
+def _bands(H: int, threads: int | None):
+    n = max(1, min(threads or 1, H))
+    edges = np.linspace(0, H, n + 1).astype(int)
+    return [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+
+
+def shade(scr, tris, index, attr, sh, tex=None, snap=None, threads: int | None = None):
+    """Shaded image [H,W,C] f64; ``snap`` (snapped coordinates) is needed for a back-face channel.  With
+    ``threads`` > 1 the rows are shaded in bands on a thread pool (the same values)."""
     H, W = index.shape
     attr = np.ascontiguousarray(attr, dtype=np.float32)
     tex = None if tex is None else np.ascontiguousarray(tex, dtype=np.float32)
     bg = np.ascontiguousarray(sh.bg_array())
     s = shading(sh, attr.shape[1], tex)
     img = np.empty((H, W, sh.C))
-    rc = lib().orc_shade(_p(scr), _p(None if snap is None else np.ascontiguousarray(snap, dtype=np.int64)),
-                         _p(np.ascontiguousarray(tris, dtype=np.int32)),
-                         _p(np.ascontiguousarray(index, dtype=np.int32)), H, W, _p(attr), _p(tex), _p(bg),
-                         ctypes.byref(s), _p(img))
-    assert rc == 0
+    snap_c = None if snap is None else np.ascontiguousarray(snap, dtype=np.int64)
+    tris_c = np.ascontiguousarray(tris, dtype=np.int32)
+    index_c = np.ascontiguousarray(index, dtype=np.int32)
+
+    def band(rows):
+        return lib().orc_shade_rows(_p(scr), _p(snap_c), _p(tris_c), _p(index_c), H, W, _p(attr), _p(tex), _p(bg),
+                                    ctypes.byref(s), _p(img), rows[0], rows[1])
+
+    bands = _bands(H, threads)
+    if len(bands) == 1:
+        rcs = [band(bands[0])]
+    else:
+        with _pool(len(bands)) as ex:
+            rcs = list(ex.map(band, bands))
+    assert all(rc == 0 for rc in rcs)
     return img
 
 
 def backward(scr, snap, flags, tris, index, image, grad_image, attr, sh, tex=None,
-             mode: int = EDGE | INTERIOR | INTERSECT, want_attr: bool = False, want_abs: bool = False):
+             mode: int = EDGE | INTERIOR | INTERSECT, want_attr: bool = False, want_abs: bool = False,
+             threads: int | None = None):
     """-> grad_scr [V,3] f64, grad_attr [V,C_attr] or None, counts dict (+ grad_abs [V,3] if want_abs:
-    the sum of the absolute values of every per-pixel contribution, the conditioning of each sum)."""
+    the sum of the absolute values of every per-pixel contribution, the conditioning of each sum).  With
+    ``threads`` > 1 bands of rows run on a thread pool, each into its own sums, added at the end (the same
+    result up to the order of the FP64 additions)."""
     H, W = index.shape
     V = len(scr)
     attr = np.ascontiguousarray(attr, dtype=np.float32)
     tex = None if tex is None else np.ascontiguousarray(tex, dtype=np.float32)
     image = np.ascontiguousarray(image, dtype=np.float64)
     grad_image = np.ascontiguousarray(grad_image, dtype=np.float32)
+    tris_c = np.ascontiguousarray(tris, dtype=np.int32)
+    index_c = np.ascontiguousarray(index, dtype=np.int32)
     s = shading(sh, attr.shape[1], tex)
-    gs = np.zeros((V, 3))
-    ga = np.zeros((V, attr.shape[1])) if want_attr else None
-    counts = np.zeros(6, np.int64)
-    gabs = np.zeros((V, 3)) if want_abs else None
-    gaabs = np.zeros((V, attr.shape[1])) if (want_abs and want_attr) else None
-    rc = lib().orc_backward(_p(scr), _p(snap), _p(flags), V, _p(np.ascontiguousarray(tris, dtype=np.int32)),
-                            _p(np.ascontiguousarray(index, dtype=np.int32)), H, W, _p(image), _p(grad_image),
-                            _p(attr), _p(tex), ctypes.byref(s), mode, _p(gs), _p(ga), _p(counts), _p(gabs),
-                            _p(gaabs))
-    assert rc == 0
+
+    def band(rows):
+        gs = np.zeros((V, 3))
+        ga = np.zeros((V, attr.shape[1])) if want_attr else None
+        counts = np.zeros(6, np.int64)
+        gabs = np.zeros((V, 3)) if want_abs else None
+        gaabs = np.zeros((V, attr.shape[1])) if (want_abs and want_attr) else None
+        rc = lib().orc_backward_rows(_p(scr), _p(snap), _p(flags), V, _p(tris_c), _p(index_c), H, W, _p(image),
+                                     _p(grad_image), _p(attr), _p(tex), ctypes.byref(s), mode, _p(gs), _p(ga),
+                                     _p(counts), _p(gabs), _p(gaabs), rows[0], rows[1])
+        assert rc == 0
+        return gs, ga, counts, gabs, gaabs
+
+    bands = _bands(H, threads)
+    if len(bands) == 1:
+        parts = [band(bands[0])]
+    else:
+        with _pool(len(bands)) as ex:
+            parts = list(ex.map(band, bands))
+    gs, ga, counts, gabs, gaabs = parts[0]
+    for p in parts[1:]:
+        gs += p[0]
+        if want_attr:
+            ga += p[1]
+        counts += p[2]
+        if want_abs:
+            gabs += p[3]
+            if want_attr:
+                gaabs += p[4]
     names = ["differing", "overhang", "adjacent", "intersection", "intersection_parallel", "intersection_off"]
     if want_abs:
         cnt = dict(zip(names, counts.tolist()))
@@ -297,12 +343,12 @@ class ViewResult:
     __slots__ = ("scr", "snap", "flags", "index", "tie", "lam", "bary", "depth", "image", "texamb", "texamb64")
 
 
-def render_view(verts, tris, cam, H, W, attr, sh, tex=None) -> ViewResult:
+def render_view(verts, tris, cam, H, W, attr, sh, tex=None, threads: int | None = None) -> ViewResult:
     r = ViewResult()
     r.scr, r.snap, r.flags = project(verts, cam)
     r.index, r.tie, _ = rasterize(r.scr, r.snap, r.flags, tris, H, W)
     r.lam, r.bary, r.depth = pixel_values(r.scr, tris, r.index)
-    r.image = shade(r.scr, tris, r.index, attr, sh, tex, r.snap)
+    r.image = shade(r.scr, tris, r.index, attr, sh, tex, r.snap, threads=threads)
     r.texamb = texel_ambiguity(r.scr, tris, r.index, attr, sh, tex)
     r.texamb64 = texel_ambiguity(r.scr, tris, r.index, attr, sh, tex, FP64_ULP)
     return r

@@ -237,7 +237,7 @@ def autotune_tile(make_renderer, run_step, candidates=(16, 32, 64), reps: int = 
     return best, times
 
 
-def autotune(make_renderer, run_step, tiles=(16, 32, 64), ctas_per_sm=(2, 4), reps: int = 3, key: str | None = None,
+def autotune(make_renderer, run_step, tiles=(16, 32, 64), ctas_per_sm=(1, 2, 4), reps: int = 3, key: str | None = None,
              cache_file: str | None = _CACHE_FILE) -> tuple[int, int, dict]:
     """Bin tile size and work split (persistent CTAs of the raster and backward grids) by timing one step per
     candidate pair -> (tile, persistent CTAs, {"tile/ctas": ms}).  make_renderer(tile, ctas) builds a

@@ -1,12 +1,17 @@
 """Data-parallel sharding over ranks, one process per GPU.
 
 Views of a mesh and the meshes of an uneven batch are independent units of the path: a rank renders and
-differentiates its own units and never reads another rank's data, so the data path has no collective.  The
-ranks meet only at the timing barrier and at the max-reduction of the measured step time.
+differentiates its own units and never reads another rank's data.
 
-Weak scaling: every rank gets the same amount of work as a single GPU would (its own 32 views; its LPT share of
-a batch of ``world x n_items`` meshes), so the whole-job throughput is the units of all ranks over the slowest
-rank's time.
+* Independent units (weak scaling): every rank gets the same amount of work as a single GPU would (its own 32
+  views; its LPT share of a batch of ``world x n_items`` meshes); the data path has no collective, the ranks
+  meet only at the timing barrier and at the max-reduction of the measured step time, and the whole-job
+  throughput is the units of all ranks over the slowest rank's time.
+* One mesh seen by many views (strong scaling): the views are split over the ranks (``split_views``), each rank
+  computes the world-space vertex gradient of its own views, and one sum over the ranks (``sum_over_ranks``,
+  an all-reduce of the [V, 3] gradient, 786 KB for the head mesh) gives every rank the gradient of all views:
+  the sum over views is the only coupling of the path (the edge and interior terms are local to each view's
+  pixels, Sec. 4.1).
 """
 from __future__ import annotations
 
@@ -74,3 +79,27 @@ def barrier() -> None:
 
     if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
         dist.barrier()
+
+
+def split_views(n_views: int, world: int) -> list[list[int]]:
+    """Contiguous split of a mesh's views over ``world`` ranks; shard sizes differ by at most one, the first
+    ``n_views % world`` ranks taking the larger ones."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    q, r = divmod(n_views, world)
+    out, start = [], 0
+    for k in range(world):
+        size = q + (1 if k < r else 0)
+        out.append(list(range(start, start + size)))
+        start += size
+    return out
+
+
+def sum_over_ranks(t):
+    """Sums tensor ``t`` over all ranks in place (an all-reduce; NCCL on GPU tensors, gloo on CPU ones) and
+    returns it; identity without a process group."""
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t

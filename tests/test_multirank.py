@@ -1,6 +1,7 @@
 """The N > 1 path on the CPU: sharding of views and uneven meshes over ranks, and the rank handshake (gloo,
-world size 2).  The data path has no collective; the ranks meet only at the timing barrier and at the
-max-reduction of the step time, so these tests cover all of the multi-rank logic."""
+world size 2).  Independent units need no collective (the ranks meet only at the timing barrier and at the
+max-reduction of the step time); one mesh seen by views split over the ranks needs one sum of the world-space
+vertex gradient over the ranks, checked here against the single-process gradient of all views."""
 from __future__ import annotations
 
 import itertools
@@ -126,3 +127,59 @@ def test_view_seeds_differ_per_rank():
     a = scenes.cameras_on_sphere(4, 3.0, 64, 48, seed=shard.view_seed(6, 0))
     b = scenes.cameras_on_sphere(4, 3.0, 64, 48, seed=shard.view_seed(6, 1))
     assert not np.array_equal(a["R"], b["R"])
+
+
+def test_split_views_covers_every_view_once():
+    for n, world in [(32, 1), (32, 2), (32, 3), (32, 8), (5, 8), (0, 2)]:
+        parts = shard.split_views(n, world)
+        assert len(parts) == world
+        assert [v for p in parts for v in p] == list(range(n))
+        sizes = [len(p) for p in parts]
+        assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        shard.split_views(4, 0)
+
+
+def _mesh_worker(rank: int, world: int, port: int, out_dir: str):
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w, r, _ = shard.env_ranks()
+    sc = scenes.head_multiview(n_views=5, H=40, W=36, n=6, tex_size=32)
+    mine = shard.split_views(sc.n_views, w)[r]
+    ovs = oracle.render(sc, mine)
+    g = sc.upstream()
+    # this rank's views only: their world-space vertex gradient, then the sum over the ranks
+    _, gw, _, _ = oracle.backward_scene(sc, ovs, [g[v] for v in mine], mine)
+    t = torch.from_numpy(gw.copy())
+    shard.sum_over_ranks(t)
+    np.save(os.path.join(out_dir, f"mesh_rank{r}.npy"), t.numpy())
+    with open(os.path.join(out_dir, f"mesh_rank{r}.json"), "w") as f:
+        json.dump({"mine": mine}, f)
+    dist.destroy_process_group()
+
+
+def test_two_rank_shared_mesh_gradient_sum(tmp_path):
+    """One mesh, five views split over two gloo ranks: after the sum over the ranks both hold the same world
+    gradient, equal to the single-process gradient of all five views (up to the order of the FP64 sums)."""
+    import torch.multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    world = 2
+    mp.spawn(_mesh_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    parts = [json.load(open(tmp_path / f"mesh_rank{r}.json"))["mine"] for r in range(world)]
+    assert parts == [[0, 1, 2], [3, 4]]
+    got = [np.load(tmp_path / f"mesh_rank{r}.npy") for r in range(world)]
+    np.testing.assert_array_equal(got[0], got[1])
+    sc = scenes.head_multiview(n_views=5, H=40, W=36, n=6, tex_size=32)
+    ovs = oracle.render(sc)
+    _, gw, _, _ = oracle.backward_scene(sc, ovs, list(sc.upstream()))
+    assert np.abs(gw).max() > 0
+    np.testing.assert_allclose(got[0], gw, rtol=1e-12, atol=1e-12 * np.abs(gw).max())

@@ -938,3 +938,39 @@ def test_world_condition_matches_finite_difference_jacobian(orc):
         gw += orc.project_backward(sc.verts, sc.cams[v], g)
     np.testing.assert_allclose(Sw, ref, rtol=1e-6, atol=1e-9)
     assert np.all(np.abs(gw) <= Sw * (1 + 1e-9) + 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# banded evaluation (test infrastructure for the long oracle-driven loops)
+# ---------------------------------------------------------------------------
+
+def test_banded_shading_and_backward_equal_the_whole_view(orc):
+    """Shading and the backward in bands of rows on several threads give the whole-view results: the image bit
+    for bit, the gradients up to the order of the FP64 sums, the pair counts exactly."""
+    sc = scenes.two_spheres(H=96, W=80, subdiv=3)
+    r = orc.render_view(sc.verts, sc.tris, sc.cams[0], sc.H, sc.W, sc.attr, sc.shading)
+    r5 = orc.render_view(sc.verts, sc.tris, sc.cams[0], sc.H, sc.W, sc.attr, sc.shading, threads=5)
+    np.testing.assert_array_equal(r.image, r5.image)
+    g = sc.upstream()[0]
+    a = orc.backward(r.scr, r.snap, r.flags, sc.tris, r.index, r.image, g, sc.attr, sc.shading, want_attr=True,
+                     want_abs=True)
+    b = orc.backward(r.scr, r.snap, r.flags, sc.tris, r.index, r.image, g, sc.attr, sc.shading, want_attr=True,
+                     want_abs=True, threads=7)
+    np.testing.assert_allclose(b[0], a[0], rtol=1e-12, atol=1e-12 * np.abs(a[0]).max())
+    np.testing.assert_allclose(b[1], a[1], rtol=1e-12, atol=1e-12 * np.abs(a[1]).max())
+    np.testing.assert_allclose(b[3], a[3], rtol=1e-12)
+    assert {k: v for k, v in a[2].items() if k != "grad_attr_abs"} == \
+        {k: v for k, v in b[2].items() if k != "grad_attr_abs"}
+    assert a[2]["intersection"] > 0
+
+
+def test_oracle_loop_normals_match_independent_formula():
+    """The oracle-driven loop's FP64 vertex normals equal the input generator's numpy normals."""
+    import torch
+
+    from oracle.fitloop import vertex_normals_fp64
+
+    sc = scenes.tiny_icosphere()
+    a = vertex_normals_fp64(torch.from_numpy(sc.verts).double(), torch.from_numpy(sc.tris).long()).numpy()
+    b = scenes.vertex_normals(sc.verts.astype(np.float64), sc.tris)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
