@@ -35,13 +35,17 @@ constexpr int kStatusFixed = 4;  // a deterministic-mode contribution beyond the
 constexpr int kBwdTileW = 32, kBwdTileH = 16;
 
 // Per (view, triangle) raster record written by the binning pass, 64 bytes.
+// A small triangle (flag bit 4: snapped box extent below 2^14) keeps its three edge functions instead of its
+// vertices: with s the sign of the area and tl_i the top-left bit of edge i, X[i] x + Y[i] y + K[i] equals
+// s e_i(pixel centre of (x, y)) + tl_i - 1 modulo 2^32 for pixel indices (x, y), and inside the box that value
+// fits 31 bits, so the wrapped 32-bit evaluation is exact and the centre is covered iff all three are >= 0.
 struct TriRaster {
-    int X[3], Y[3];   // snapped vertex positions
+    int X[3], Y[3];   // snapped vertex positions; small triangle: edge i's coefficients of x and y
     float zd[3];      // zeta_i / |E_0 + E_1 + E_2|, FP32
     int flags;        // bits 0..2: edge i is top-left; bit 3: negative area; bit 4: small (32-bit path); bit 31: culled
     short bx0, bx1, by0, by1;  // inclusive pixel bounding box of the covered centres
     float zmax;       // largest vertex zeta: no fragment of the triangle has a larger depth key
-    int pad[3];
+    int K[3];         // small triangle: edge i's constant term (unused otherwise)
 };
 static_assert(sizeof(TriRaster) == 64, "TriRaster");
 
@@ -102,18 +106,17 @@ __device__ __forceinline__ bool covers(const TriRaster& t, int px, int py, int64
     return true;
 }
 
-// The same predicate for a "small" triangle (snapped bbox extent < 2^14): every factor is then below 2^15
-// in magnitude for a pixel inside the bbox, so each product fits 30 bits and the edge function 31 bits.
-__device__ __forceinline__ bool covers_small(const TriRaster& t, int px, int py, int E[3]) {
-    const bool neg = (t.flags & 8) != 0;
+// The same predicate for a "small" triangle (snapped bbox extent < 2^14) at the centre of pixel (x, y) inside
+// its box, from the record's edge functions: |e_i| < 2^29 there, so the wrapped evaluation is exact.  E[i] is
+// s e_i, as covers would give it after the sign flip.
+__device__ __forceinline__ bool covers_small(const TriRaster& t, int x, int y, int E[3]) {
+    int e[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const int j = (i + 1) % 3, k = (i + 2) % 3;
-        int e = (t.X[j] - px) * (t.Y[k] - py) - (t.Y[j] - py) * (t.X[k] - px);
-        if (neg) e = -e;
-        E[i] = e;
-        if (e + ((t.flags >> i) & 1) <= 0) return false;
-    }
+    for (int i = 0; i < 3; ++i)
+        e[i] = (int)((unsigned)t.K[i] + (unsigned)t.X[i] * (unsigned)x + (unsigned)t.Y[i] * (unsigned)y);
+    if ((e[0] | e[1] | e[2]) < 0) return false;  // covered iff s e_i + tl_i > 0 for every edge
+#pragma unroll
+    for (int i = 0; i < 3; ++i) E[i] = e[i] + 1 - ((t.flags >> i) & 1);
     return true;
 }
 

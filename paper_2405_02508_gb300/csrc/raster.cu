@@ -94,13 +94,35 @@ __device__ __forceinline__ void setup_count_one(const RItem& it, int t, int tile
         const int64_t gb = (int64_t)s * (r.X[k] - r.X[j]);
         if (ga > 0 || (ga == 0 && gb > 0)) fl |= 1 << e;
     }
-    if (mxx - mnx < (1 << 14) && mxy - mny < (1 << 14)) fl |= 16;  // small: exact 32-bit coverage
+    const bool small = mxx - mnx < (1 << 14) && mxy - mny < (1 << 14);
+    if (small) fl |= 16;  // small: exact 32-bit coverage from the edge functions
     r.flags = fl;
     const float Df = ll2f_rn(a2 < 0 ? -a2 : a2);
 #pragma unroll
     for (int k = 0; k < 3; ++k) r.zd[k] = __fdiv_rn(v[k].zeta, Df);
     r.zmax = fmaxf(v[0].zeta, fmaxf(v[1].zeta, v[2].zeta));
     r.bx0 = (short)x0; r.bx1 = (short)x1; r.by0 = (short)y0; r.by1 = (short)y1;
+    r.K[0] = r.K[1] = r.K[2] = 0;
+    if (small) {
+        // s e_i(P) = s (X_j Y_k - Y_j X_k) + s (Y_j - Y_k) P_x + s (X_k - X_j) P_y with P = 256 (x, y) + 128:
+        // coefficients of the pixel indices and the constant with tl_i - 1 folded in, all modulo 2^32
+        int ex[3], ey[3], ek[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int j = (e + 1) % 3, k = (e + 2) % 3;
+            const unsigned A = (unsigned)(s * (r.Y[j] - r.Y[k])), B = (unsigned)(s * (r.X[k] - r.X[j]));
+            const unsigned c = (unsigned)r.X[j] * (unsigned)r.Y[k] - (unsigned)r.Y[j] * (unsigned)r.X[k];
+            ex[e] = (int)(256u * A);
+            ey[e] = (int)(256u * B);
+            ek[e] = (int)((s > 0 ? c : 0u - c) + 128u * A + 128u * B + (unsigned)((fl >> e) & 1) - 1u);
+        }
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            r.X[e] = ex[e];
+            r.Y[e] = ey[e];
+            r.K[e] = ek[e];
+        }
+    }
     it.recs[t] = r;
     int* cnt = counts + it.tile0;
     if (y0 / tile == y1 / tile && x0 / tile == x1 / tile) {
@@ -333,7 +355,7 @@ __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, con
                 float z;
                 if (r.flags & 16) {
                     int E[3];
-                    if (!covers_small(r, 256 * px + 128, 256 * py + 128, E)) continue;
+                    if (!covers_small(r, px, py, E)) continue;
                     z = depth_key_small(r, E);
                 } else {
                     int64_t E[3];
