@@ -340,10 +340,13 @@ __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, con
             if (bw <= 0 || bh <= 0) continue;
             const int npx = bw * bh;
             const unsigned idkey = 0xFFFFFFFFu - (unsigned)S.id[j];
-            // lane -> (dx, dy) in the bbox, then advance by 32 pixels per pass without dividing per pixel
-            int dy = lane / bw;
+            // lane -> (dx, dy) in the bbox, then advance by 32 pixels per pass without dividing per pixel.  The
+            // quotients q / bw (q <= 32, bw <= TS <= 64) come from an approximate reciprocal: the product is within
+            // 2^-16 of q / bw, whose fraction is 0 or at least 1/64, so q / bw + 2^-10 truncates to the quotient.
+            const float rb = __fdividef(1.0f, (float)bw);
+            int dy = (int)__fmaf_rn((float)lane, rb, 0x1p-10f);
             int dx = lane - dy * bw;
-            const int sy = 32 / bw, sx = 32 - sy * bw;
+            const int sy = (int)__fmaf_rn(32.0f, rb, 0x1p-10f), sx = 32 - sy * bw;
             for (int i = lane; i < npx; i += 32) {
                 const int px = x0 + dx, py = y0 + dy;
                 dx += sx;
