@@ -245,6 +245,7 @@ __global__ void k_scan_add(int* __restrict__ out, long long N, const int* __rest
 // (depth key bits << 32 | ~triangle id): larger depth key wins, equal keys go to the lower id.
 constexpr int kStage = 256;  // triangle records staged per round
 constexpr int kRasterThreads = 256;
+constexpr int kRasterCtasPerSm = 4;  // resident CTAs per SM (the 64 x 64 tile's shared memory allows four): 64 registers
 
 // Per-pixel bits kept in shared memory for the cover image: a front-facing triangle covered the centre
 // (taken when the front part is done), two or more did, one / two or more back-facing ones did, and a
@@ -332,7 +333,7 @@ __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, con
         __syncthreads();
         const bool back = base >= nf;
         for (int j = warp; j < m; j += kWarps) {
-            const TriRaster& r = S.rec[j];
+            const TriRaster r = S.rec[j];  // in registers: the loop's shared-memory atomics would force reloads
             if (back && r.zmax * (1.0f + 0x1p-20f) < zcull) continue;  // hidden behind the whole tile
             const int x0 = max((int)r.bx0, ox), x1 = min((int)r.bx1, ox + TS - 1);
             const int y0 = max((int)r.by0, oy), y1 = min((int)r.by1, oy + TS - 1);
@@ -470,7 +471,7 @@ __global__ void k_bin_fill(const mer_vertex* __restrict__ vpix, const int* __res
 }
 
 template <int TS>
-__global__ void __launch_bounds__(kRasterThreads) k_raster(TriRaster* __restrict__ recs, BinGeom g,
+__global__ void __launch_bounds__(kRasterThreads, kRasterCtasPerSm) k_raster(TriRaster* __restrict__ recs, BinGeom g,
                                                            const int* __restrict__ offs, const int* __restrict__ cnts,
                                                            const int* __restrict__ nfront,
                                                            const int* __restrict__ list, const mer_vertex* __restrict__ vpix,
@@ -534,7 +535,7 @@ __global__ void k_bin_fill_batch(const mer_vertex* __restrict__ vpix, const int*
 
 // Persistent: each CTA takes the next global tile from the work queue until none is left.
 template <int TS, bool SHADE>
-__global__ void __launch_bounds__(kRasterThreads) k_raster_batch(TriRaster* __restrict__ recs, BatchGeom b,
+__global__ void __launch_bounds__(kRasterThreads, kRasterCtasPerSm) k_raster_batch(TriRaster* __restrict__ recs, BatchGeom b,
                                                                  const int* __restrict__ offs,
                                                                  const int* __restrict__ cnts,
                                                                  const int* __restrict__ nfront,
