@@ -118,8 +118,8 @@ class ClockSampler:
 # one k_backward_batch launch, from an ncu capture of the same workload at 4 views (inputs already larger than
 # L2), per pixel of the launch, with the sha256 of the kernel's sources they were taken on: a launch of n views
 # moves / issues n*H*W times these.  They are reported only while the sources are unchanged.
-BACKWARD_TRAFFIC = {"bytes_per_pixel": 26.7856, "warp_instructions_per_pixel": 37.1680,
-                    "sources_sha256": "1fd40bfe4e979b7343e190a8ec1645ee7e6ae86fd2a2859e908221bf79d2a984",
+BACKWARD_TRAFFIC = {"bytes_per_pixel": 26.7181, "warp_instructions_per_pixel": 33.6038,
+                    "sources_sha256": "d0095ba0d4b693ba036f9d726b64a6c4e0b5e0f1ebf0ffb545d191d2facd31e7",
                     "profile": "profiles/ncu_k_backward_batch_head_4x1334x2048.md"}
 
 
