@@ -50,6 +50,16 @@ struct TriTable {
 };
 
 struct BwdArgs {
+    // base pointers of the launch's arrays (an item addresses them through its offsets)
+    const mer_vertex* vpix;
+    const int* tris;
+    const int* index;
+    const unsigned char* cover;  // or null
+    const float* image;
+    const float* grad;
+    const float* attr;
+    double* grad_vpix;
+    float* grad_attr;            // or null
     mer_shading sh;
     int terms;
     int n, H, W, V, T;
@@ -102,18 +112,23 @@ __device__ __forceinline__ int table_slot(int* keys, int key) {
     return -1;
 }
 
-// One item of a backward pass: a mesh seen by one camera, bases of all its arrays.
+// One item of a backward pass: a mesh seen by one camera, as offsets into the launch's arrays (kept instead of
+// nine pointers: fewer registers live across the pixel pass; the bases are kernel parameters).
 struct BItem {
-    const mer_vertex* vb;   // vertex records
-    const int* tris;        // triangles (item-local vertex ids)
-    const int* index;       // index image [H, W]
-    const unsigned char* cover;  // cover image [H, W] (MER_COVER_* bits) or null
-    const float* image;     // shaded image [H, W, C]
-    const float* grad;      // dL/d image [H, W, C]
-    const float* attr;      // attributes [V, C_attr]
-    double* gv;             // grad_vpix [V, 3]
-    float* gattr;           // grad_attr [V, C_attr] or null
+    long long vrec;  // first vertex record (and grad_vpix row)
+    long long tri;   // first triangle
+    long long pix;   // first pixel of the index, cover, image and gradient images
+    long long vert;  // first attribute (and grad_attr) row
     int V, T, H, W;
+    __device__ __forceinline__ const mer_vertex* vb(const BwdArgs& a) const { return a.vpix + vrec; }
+    __device__ __forceinline__ const int* tris(const BwdArgs& a) const { return a.tris + 3 * tri; }
+    __device__ __forceinline__ const int* index(const BwdArgs& a) const { return a.index + pix; }
+    __device__ __forceinline__ const unsigned char* cover(const BwdArgs& a) const { return a.cover + pix; }
+    __device__ __forceinline__ const float* image(const BwdArgs& a) const { return a.image + pix * a.sh.C; }
+    __device__ __forceinline__ const float* grad(const BwdArgs& a) const { return a.grad + pix * a.sh.C; }
+    __device__ __forceinline__ const float* attr(const BwdArgs& a) const { return a.attr + vert * a.sh.C_attr; }
+    __device__ __forceinline__ double* gv(const BwdArgs& a) const { return a.grad_vpix + 3 * vrec; }
+    __device__ __forceinline__ float* gattr(const BwdArgs& a) const { return a.grad_attr + vert * a.sh.C_attr; }
 };
 
 constexpr int kMaxA = 4;  // most attribute-gradient channels carried through the per-tile aggregation
@@ -146,7 +161,7 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
     unsigned m[kM];  // per (row k, direction d): lanes whose pixel is covered and whose neighbour in d differs
     int np[kM + 1];  // prefix counts
     np[0] = 0;
-    const bool hinted = it.cover != nullptr;
+    const bool hinted = a.cover != nullptr;
 #pragma unroll
     for (int k = 0; k < kRows; ++k) {
         const int row = r0 + k;
@@ -193,7 +208,7 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
         }
     }
     __syncwarp();
-    const mer_vertex* vb = it.vb;
+    const mer_vertex* vb = it.vb(a);
     for (int i = lane; i < n; i += 32) {
         // list entry i -> mask s (the last one whose prefix count is <= i), its row, direction and source lane
         int s = 0;
@@ -218,7 +233,7 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
         int vs[3] = {0, 0, 0};
         int Xs[3] = {0, 0, 0}, Ys[3] = {0, 0, 0};
         if (tq >= 0 || EXACT) {  // a pair against the background needs only Eq. 11 (the row pass checks ts)
-            if (ts >= it.T || !tri_ids(it.tris, ts, it.V, vs)) {
+            if (ts >= it.T || !tri_ids(it.tris(a), ts, it.V, vs)) {
                 set_status(ws, kStatusRange);
                 continue;
             }
@@ -234,7 +249,7 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
         bool inter = false;
         int vq[3] = {0, 0, 0};
         if (tq >= 0) {
-            if (tq >= it.T || !tri_ids(it.tris, tq, it.V, vq)) {
+            if (tq >= it.T || !tri_ids(it.tris(a), tq, it.V, vq)) {
                 set_status(ws, kStatusRange);
                 continue;
             }
@@ -276,7 +291,7 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
         // Eq. 11 with A = left/top pixel, B = right/bottom pixel
         const size_t p = (size_t)y * it.W + px;
         const size_t q = (size_t)qy * it.W + qx;
-        const float *gp = it.grad + p * C, *gq = it.grad + q * C, *ip = it.image + p * C, *iq = it.image + q * C;
+        const float *gp = it.grad(a) + p * C, *gq = it.grad(a) + q * C, *ip = it.image(a) + p * C, *iq = it.image(a) + q * C;
         const bool p_is_a = ddx > 0 || ddy > 0;
         float dLdp = 0.f;
         for (int c = 0; c < C; ++c) {
@@ -349,15 +364,16 @@ __device__ __forceinline__ void table_clear(BwdShared<NA, EXACT, BITS>& S) {
 
 // Returns whether this thread loaded a covered pixel of the tile itself (not the halo).
 template <int NA, bool EXACT, int BITS>
-__device__ __forceinline__ bool tile_halo(const BItem& it, int tx, int ty, BwdShared<NA, EXACT, BITS>& S) {
+__device__ __forceinline__ bool tile_halo(const BItem& it, const BwdArgs& a, int tx, int ty,
+                                          BwdShared<NA, EXACT, BITS>& S) {
     bool covered = false;
     for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
         const int hy = i / kHW, hx = i % kHW;
         const int gx = tx * kTW + hx - 1, gy = ty * kTH + hy - 1;
         const bool in = gx >= 0 && gx < it.W && gy >= 0 && gy < it.H;
-        const int v = in ? __ldg(it.index + (size_t)gy * it.W + gx) : -2;
+        const int v = in ? __ldg(it.index(a) + (size_t)gy * it.W + gx) : -2;
         S.sidx[hy][hx] = v;
-        if (it.cover) S.scov[hy][hx] = in ? __ldg(it.cover + (size_t)gy * it.W + gx) : (unsigned char)0;
+        if (a.cover) S.scov[hy][hx] = in ? __ldg(it.cover(a) + (size_t)gy * it.W + gx) : (unsigned char)0;
         covered |= v >= 0 && hy >= 1 && hy <= kTH && hx >= 1 && hx <= kTW;
     }
     return covered;
@@ -375,11 +391,11 @@ __device__ __forceinline__ void row_pass(const BItem& it, int tx, int ty, int ro
     const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
     const int x = tx * kTW + lane, y = ty * kTH + row;
     const int C = a.sh.C;
-    const mer_vertex* vb = it.vb;
-    const int* tris = it.tris;
-    const float* grad = it.grad;
-    const float* attr = it.attr;
-    float* grad_attr = it.gattr;
+    const mer_vertex* vb = it.vb(a);
+    const int* tris = it.tris(a);
+    const float* grad = it.grad(a);
+    const float* attr = it.attr(a);
+    float* grad_attr = it.gattr(a);
     int t = (x < it.W && y < it.H) ? S.sidx[row + 1][lane + 1] : -1;
     if (!__any_sync(0xffffffffu, t >= 0)) return;  // background row: no fragment, no pair
     int vid[3] = {0, 0, 0};
@@ -547,7 +563,7 @@ __device__ __forceinline__ void row_pass(const BItem& it, int tx, int ty, int ro
     }
     const int tnext = __shfl_down_sync(full, t, 1);
     const bool tail = lane == 31 || tnext != t;
-    double* gvv = it.gv;
+    double* gvv = it.gv(a);
     if (tail && t >= 0 && any) {
         // one slot per triangle: the runs of one row hold different triangles, so their adds do not contend
         const int sl = table_slot<TriTable<NA, EXACT, BITS>::kBits>(S.skey, t);
@@ -593,7 +609,8 @@ template <int NA, bool EXACT, int BITS>
 __device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, BwdShared<NA, EXACT, BITS>& S) {
     const int A = a.sh.uv_offset < 0 ? a.sh.n_main : 2;
     const int a0 = a.sh.uv_offset < 0 ? 0 : a.sh.uv_offset;
-    double* gvv = it.gv;
+    double* gvv = it.gv(a);
+    float* gattr = it.gattr(a);
     for (int i = threadIdx.x; i < S.kSlots; i += kThreads) {
         if (S.skey[i] < 0) continue;
         S.skey[i] = -1;
@@ -613,7 +630,7 @@ __device__ __forceinline__ void tile_flush(const BItem& it, const BwdArgs& a, Bw
                     if (j >= A) break;
                     const float sa = S.sattr[i][k][j];
                     S.sattr[i][k][j] = 0.f;
-                    if (sa != 0.f) atomicAdd(it.gattr + (size_t)v * a.sh.C_attr + a0 + j, sa);
+                    if (sa != 0.f) atomicAdd(gattr + (size_t)v * a.sh.C_attr + a0 + j, sa);
                 }
             }
         }
@@ -635,18 +652,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward(const mer_ver
     const int local = blockIdx.x % tiles_per_view;
     const size_t plane = (size_t)a.H * a.W;
     BItem it;
-    it.vb = vpix + (size_t)view * a.V;
-    it.tris = tris;
-    it.index = index + (size_t)view * plane;
-    it.cover = cover ? cover + (size_t)view * plane : nullptr;
-    it.image = image ? image + (size_t)view * plane * a.sh.C : nullptr;
-    it.grad = grad + (size_t)view * plane * a.sh.C;
-    it.attr = attr;
-    it.gv = grad_vpix + (size_t)view * a.V * 3;
-    it.gattr = grad_attr;
+    it.vrec = (long long)view * a.V;
+    it.tri = 0;
+    it.pix = (long long)view * (long long)plane;
+    it.vert = 0;
     it.V = a.V; it.T = a.T; it.H = a.H; it.W = a.W;
     table_clear(S);
-    const bool covered = tile_halo(it, local % a.ntx, local / a.ntx, S);
+    const bool covered = tile_halo(it, a, local % a.ntx, local / a.ntx, S);
     if (!__syncthreads_or(covered)) return;  // background tile
     tile_compute<NA, EXACT, BITS>(it, local % a.ntx, local / a.ntx, a, tex, S, ws);
     __syncthreads();
@@ -669,7 +681,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward_batch(const m
     __shared__ BwdShared<NA, EXACT, BITS> S;
     __shared__ long long s_tile;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
-    const int C = a.sh.C, Ca = a.sh.C_attr;
     table_clear(S);
     if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_backward, 1ull);
     __syncthreads();
@@ -693,18 +704,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_backward_batch(const m
         const int ntx = (m.W + kTW - 1) / kTW;
         const int local = (int)(g - m.btile);
         BItem it;
-        it.vb = vpix + m.vrec;
-        it.tris = tris + 3 * m.tri;
-        it.index = index + m.pix;
-        it.cover = cover ? cover + m.pix : nullptr;
-        it.image = image ? image + (size_t)m.pix * C : nullptr;
-        it.grad = grad + (size_t)m.pix * C;
-        it.attr = attr ? attr + (size_t)m.vert * Ca : nullptr;
-        it.gv = grad_vpix + 3 * (size_t)m.vrec;
-        it.gattr = grad_attr ? grad_attr + (size_t)m.vert * Ca : nullptr;
+        it.vrec = m.vrec;
+        it.tri = m.tri;
+        it.pix = m.pix;
+        it.vert = m.vert;
         it.V = m.V; it.T = m.T; it.H = m.H; it.W = m.W;
         const int tx = local % ntx, ty = local / ntx;
-        tile_halo(it, tx, ty, S);
+        tile_halo(it, a, tx, ty, S);
         __syncthreads();
         if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&hdr->queue_backward, 1ull);
         tile_compute<NA, EXACT, BITS>(it, tx, ty, a, tex, S, ws);
@@ -735,6 +741,8 @@ extern "C" int mer_launch_backward_batch(const mer_vertex* vpix, const int* tris
                                          void* ws, int persistent_ctas, double max_tri_density, cudaStream_t s) {
     if (btiles == 0) return 0;
     BwdArgs a;
+    a.vpix = vpix; a.tris = tris; a.index = index; a.cover = cover; a.image = image; a.grad = grad_image;
+    a.attr = attr; a.grad_vpix = grad_vpix; a.grad_attr = grad_attr;
     a.sh = *sh;
     a.terms = terms;
     a.n = 0; a.H = 0; a.W = 0; a.V = 0; a.T = 0; a.ntx = 0; a.nty = 0;
@@ -801,6 +809,8 @@ extern "C" int mer_launch_backward(const mer_vertex* vpix, int V, const int* tri
                                    const float* tex, const mer_shading* sh, int terms, double* grad_vpix,
                                    float* grad_attr, void* ws, cudaStream_t s) {
     BwdArgs a;
+    a.vpix = vpix; a.tris = tris; a.index = index; a.cover = cover; a.image = image; a.grad = grad_image;
+    a.attr = attr; a.grad_vpix = grad_vpix; a.grad_attr = grad_attr;
     a.sh = *sh;
     a.terms = terms;
     a.n = n; a.H = H; a.W = W; a.V = V; a.T = T;
