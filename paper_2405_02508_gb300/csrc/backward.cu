@@ -362,19 +362,35 @@ __device__ __forceinline__ void table_clear(BwdShared<NA, EXACT, BITS>& S) {
     }
 }
 
-// Returns whether this thread loaded a covered pixel of the tile itself (not the halo).
+// Returns whether this thread loaded a covered pixel of the tile itself (not the halo).  Each thread issues
+// all its loads (at most three entries and their cover bytes) before it stores any.
 template <int NA, bool EXACT, int BITS>
 __device__ __forceinline__ bool tile_halo(const BItem& it, const BwdArgs& a, int tx, int ty,
                                           BwdShared<NA, EXACT, BITS>& S) {
-    bool covered = false;
-    for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
+    constexpr int kN = (kHH * kHW + kThreads - 1) / kThreads;
+    int v[kN];
+    unsigned char c[kN];
+    const int* ib = it.index(a);
+    const unsigned char* cb = a.cover ? it.cover(a) : nullptr;
+#pragma unroll
+    for (int q = 0; q < kN; ++q) {
+        const int i = threadIdx.x + q * kThreads;
         const int hy = i / kHW, hx = i % kHW;
         const int gx = tx * kTW + hx - 1, gy = ty * kTH + hy - 1;
-        const bool in = gx >= 0 && gx < it.W && gy >= 0 && gy < it.H;
-        const int v = in ? __ldg(it.index(a) + (size_t)gy * it.W + gx) : -2;
-        S.sidx[hy][hx] = v;
-        if (a.cover) S.scov[hy][hx] = in ? __ldg(it.cover(a) + (size_t)gy * it.W + gx) : (unsigned char)0;
-        covered |= v >= 0 && hy >= 1 && hy <= kTH && hx >= 1 && hx <= kTW;
+        const bool in = i < kHH * kHW && gx >= 0 && gx < it.W && gy >= 0 && gy < it.H;
+        const size_t o = in ? (size_t)gy * it.W + gx : 0;
+        v[q] = in ? __ldg(ib + o) : -2;
+        c[q] = (in && cb) ? __ldg(cb + o) : (unsigned char)0;
+    }
+    bool covered = false;
+#pragma unroll
+    for (int q = 0; q < kN; ++q) {
+        const int i = threadIdx.x + q * kThreads;
+        if (i >= kHH * kHW) break;
+        const int hy = i / kHW, hx = i % kHW;
+        S.sidx[hy][hx] = v[q];
+        if (cb) S.scov[hy][hx] = c[q];
+        covered |= v[q] >= 0 && hy >= 1 && hy <= kTH && hx >= 1 && hx <= kTW;
     }
     return covered;
 }
