@@ -118,8 +118,8 @@ class ClockSampler:
 # one k_backward_batch launch, from an ncu capture of the same workload at 4 views (inputs already larger than
 # L2), per pixel of the launch, with the sha256 of the kernel's sources they were taken on: a launch of n views
 # moves / issues n*H*W times these.  They are reported only while the sources are unchanged.
-BACKWARD_TRAFFIC = {"bytes_per_pixel": 26.7181, "warp_instructions_per_pixel": 33.6038,
-                    "sources_sha256": "d0095ba0d4b693ba036f9d726b64a6c4e0b5e0f1ebf0ffb545d191d2facd31e7",
+BACKWARD_TRAFFIC = {"bytes_per_pixel": 26.9535, "warp_instructions_per_pixel": 33.4069,
+                    "sources_sha256": "d73fc0241e69b2f19972834ff3a505308c39cb1d86eeb5fa7bdf6753c6f2d9c5",
                     "profile": "profiles/ncu_k_backward_batch_head_4x1334x2048.md"}
 
 
