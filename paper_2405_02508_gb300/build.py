@@ -2,7 +2,7 @@
 
 Each translation unit is compiled in parallel, then linked into one shared
 library next to this file.  The CUDA runtime is linked statically, so the
-library has no run-time dependency beyond the driver.
+library has no run-time dependency beyond the CUDA driver.
 """
 from __future__ import annotations
 

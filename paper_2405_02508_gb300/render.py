@@ -1,4 +1,4 @@
-"""Forward/backward driver over the C-ABI, and the ``torch.autograd.Function``.
+"""Forward/backward calls over the C-ABI, and the ``torch.autograd.Function``.
 
 ``Renderer`` owns the caller-side buffers (workspace, vertex records, images)
 for one mesh and a batch of views and chains the library calls:
