@@ -230,12 +230,14 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
         const int px = x0 + src, y = y0 + row;
         const int ts = S.sidx[row + 1][src + 1];
         const int tq = S.sidx[row + 1 + ddy][src + 1 + ddx];
+        // p's triangle: its vertex ids and snapped positions, loaded only when needed (the exact-crossing
+        // option, or a neighbour triangle that covers p's centre); false after a range error
         int vs[3] = {0, 0, 0};
         int Xs[3] = {0, 0, 0}, Ys[3] = {0, 0, 0};
-        if (tq >= 0 || EXACT) {  // a pair against the background needs only Eq. 11 (the row pass checks ts)
+        auto load_source = [&]() -> bool {
             if (ts >= it.T || !tri_ids(it.tris(a), ts, it.V, vs)) {
                 set_status(ws, kStatusRange);
-                continue;
+                return false;
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -243,46 +245,31 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
                 Xs[k] = xy.x;
                 Ys[k] = xy.y;
             }
-        }
+            return true;
+        };
+        if (EXACT && !load_source()) continue;
         const int qx = px + ddx, qy = y + ddy;
         const int axis = ddx != 0 ? 0 : 1;
         bool inter = false;
         int vq[3] = {0, 0, 0};
-        if (tq >= 0) {
+        if (tq >= 0) {  // a pair against the background needs only Eq. 11 (the row pass checks ts)
             if (tq >= it.T || !tri_ids(it.tris(a), tq, it.V, vq)) {
                 set_status(ws, kStatusRange);
                 continue;
             }
-            // Fast exit for triangles sharing an edge (the common case inside a closed mesh): q's triangle lies
-            // on the side of the shared edge where its third vertex is; p's centre strictly on the other side
-            // is outside it, so p's fragment gets nothing from this pair.
-            int nshared = 0, odd = -1, pos_in_t[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                pos_in_t[k] = vq[k] == vs[0] ? 0 : (vq[k] == vs[1] ? 1 : (vq[k] == vs[2] ? 2 : -1));
-                if (pos_in_t[k] >= 0) ++nshared; else odd = k;
-            }
             int Xq[3], Yq[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (nshared == 2 && pos_in_t[k] >= 0) {
-                    Xq[k] = Xs[pos_in_t[k]];
-                    Yq[k] = Ys[pos_in_t[k]];
-                } else {  // snapped position only: one 64-bit load per vertex
-                    const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
-                    Xq[k] = xy.x;
-                    Yq[k] = xy.y;
-                }
-            }
-            if (nshared == 2) {
-                const int j = (odd + 1) % 3, k = (odd + 2) % 3;
-                const int64_t side_d = edge_fn(Xq[j], Yq[j], Xq[k], Yq[k], Xq[odd], Yq[odd]);
-                const int64_t side_p = edge_fn(Xq[j], Yq[j], Xq[k], Yq[k], 256 * px + 128, 256 * y + 128);
-                if ((side_d > 0 && side_p < 0) || (side_d < 0 && side_p > 0)) continue;
+            for (int k = 0; k < 3; ++k) {  // snapped position only: one 64-bit load per vertex
+                const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
+                Xq[k] = xy.x;
+                Yq[k] = xy.y;
             }
             // classification (Sec. 4.3): p's fragment scatters only if p's centre lies inside q's triangle
-            // (p on top of it), or both centres lie in each other's triangles (intersection)
+            // (p on top of it), or both centres lie in each other's triangles (intersection).  Most pairs end
+            // at the first test (a neighbour sharing an edge with p's triangle lies on the far side of it), so
+            // p's triangle is loaded only after it.
             if (!covers_xy(Xq, Yq, 256 * px + 128, 256 * y + 128)) continue;
+            if (!EXACT && !load_source()) continue;
             if (covers_xy(Xs, Ys, 256 * qx + 128, 256 * qy + 128)) {
                 if (!(a.terms & MER_INTERSECT)) continue;
                 inter = true;
