@@ -143,6 +143,7 @@ struct BwdShared {
     float sval[kSlots][3][3];         // per vertex of the triangle: dL/d(x_s, y_s, zeta)
     float sattr[NA > 0 ? kSlots : 1][3][NA > 0 ? NA : 1];
     float efrag[kTH][32][3];  // per row: edge-term fragment gradients returned to the pixel's lane
+    unsigned char slist[kThreads / 32][4 * kRows * 32];  // per warp: its edge pairs kept by the first test
     float evert[EXACT ? kTH : 1][32][3][2];  // exact-crossing option: per pixel, (x, y) per triangle vertex
 };
 
@@ -209,35 +210,78 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
     }
     __syncwarp();
     const mer_vertex* vb = it.vb(a);
-    for (int i = lane; i < n; i += 32) {
-        // list entry i -> mask s (the last one whose prefix count is <= i), its row, direction and source lane
-        int s = 0;
+    // Pass 1 over the list, 32 entries at a time: the test of p's centre against q's triangle (most pairs end
+    // there) or, against the background, nothing; the surviving entries (row-direction mask s, source lane)
+    // are compacted into the warp's byte list, so that pass 2 runs the rest with its lanes full.
+    unsigned char* keep_list = S.slist[threadIdx.x >> 5];
+    int nk = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        bool keep = false;
+        int code = 0;
+        if (i < n) {
+            // list entry i -> mask s (the last one whose prefix count is <= i), its row, direction and source
+            int s = 0;
 #pragma unroll
-        for (int j = 1; j < kM; ++j)
-            if (i >= np[j]) s = j;
-        unsigned md = m[0];
-        int start = 0;
+            for (int j = 1; j < kM; ++j)
+                if (i >= np[j]) s = j;
+            unsigned md = m[0];
+            int start = 0;
 #pragma unroll
-        for (int j = 1; j < kM; ++j)
-            if (s == j) {
-                md = m[j];
-                start = np[j];
+            for (int j = 1; j < kM; ++j)
+                if (s == j) {
+                    md = m[j];
+                    start = np[j];
+                }
+            const int row = r0 + (s >> 2), d = s & 3;
+            const int src = (int)__fns(md, 0, i - start + 1);
+            const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
+            const int ddy = d == 2 ? -1 : (d == 3 ? 1 : 0);
+            const int tq = S.sidx[row + 1 + ddy][src + 1 + ddx];
+            code = (s << 5) | src;
+            keep = true;  // a pair against the background needs only Eq. 11 (the row pass checks p's triangle)
+            if (tq >= 0) {
+                int vq[3];
+                if (tq >= it.T || !tri_ids(it.tris(a), tq, it.V, vq)) {
+                    set_status(ws, kStatusRange);
+                    keep = false;
+                } else {
+                    int Xq[3], Yq[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {  // snapped position only: one 64-bit load per vertex
+                        const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
+                        Xq[k] = xy.x;
+                        Yq[k] = xy.y;
+                    }
+                    // classification (Sec. 4.3): p's fragment scatters only if p's centre lies inside q's
+                    // triangle (p on top of it), or both centres lie in each other's triangles (intersection)
+                    keep = covers_xy(Xq, Yq, 256 * (x0 + src) + 128, 256 * (y0 + row) + 128);
+                }
             }
+        }
+        const unsigned kb = __ballot_sync(full, keep);
+        if (keep) keep_list[nk + __popc(kb & ((1u << lane) - 1u))] = (unsigned char)code;
+        nk += __popc(kb);
+    }
+    __syncwarp();
+    // Pass 2 over the kept entries: the intersection test, Eq. 11 and the fragment gradient.
+    for (int i = lane; i < nk; i += 32) {
+        const int code = keep_list[i];
+        const int s = code >> 5, src = code & 31;
         const int row = r0 + (s >> 2), d = s & 3;
-        const int src = (int)__fns(md, 0, i - start + 1);
         const int ddx = d == 0 ? -1 : (d == 1 ? 1 : 0);
         const int ddy = d == 2 ? -1 : (d == 3 ? 1 : 0);
         const int px = x0 + src, y = y0 + row;
         const int ts = S.sidx[row + 1][src + 1];
         const int tq = S.sidx[row + 1 + ddy][src + 1 + ddx];
-        // p's triangle: its vertex ids and snapped positions, loaded only when needed (the exact-crossing
-        // option, or a neighbour triangle that covers p's centre); false after a range error
+        // p's triangle: its vertex ids and snapped positions (the exact-crossing option, or a neighbour
+        // triangle that covers p's centre)
         int vs[3] = {0, 0, 0};
         int Xs[3] = {0, 0, 0}, Ys[3] = {0, 0, 0};
-        auto load_source = [&]() -> bool {
+        if (EXACT || tq >= 0) {
             if (ts >= it.T || !tri_ids(it.tris(a), ts, it.V, vs)) {
                 set_status(ws, kStatusRange);
-                return false;
+                continue;
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -245,35 +289,13 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
                 Xs[k] = xy.x;
                 Ys[k] = xy.y;
             }
-            return true;
-        };
-        if (EXACT && !load_source()) continue;
+        }
         const int qx = px + ddx, qy = y + ddy;
         const int axis = ddx != 0 ? 0 : 1;
         bool inter = false;
-        int vq[3] = {0, 0, 0};
-        if (tq >= 0) {  // a pair against the background needs only Eq. 11 (the row pass checks ts)
-            if (tq >= it.T || !tri_ids(it.tris(a), tq, it.V, vq)) {
-                set_status(ws, kStatusRange);
-                continue;
-            }
-            int Xq[3], Yq[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {  // snapped position only: one 64-bit load per vertex
-                const int2 xy = __ldg(reinterpret_cast<const int2*>(vb + vq[k]));
-                Xq[k] = xy.x;
-                Yq[k] = xy.y;
-            }
-            // classification (Sec. 4.3): p's fragment scatters only if p's centre lies inside q's triangle
-            // (p on top of it), or both centres lie in each other's triangles (intersection).  Most pairs end
-            // at the first test (a neighbour sharing an edge with p's triangle lies on the far side of it), so
-            // p's triangle is loaded only after it.
-            if (!covers_xy(Xq, Yq, 256 * px + 128, 256 * y + 128)) continue;
-            if (!EXACT && !load_source()) continue;
-            if (covers_xy(Xs, Ys, 256 * qx + 128, 256 * qy + 128)) {
-                if (!(a.terms & MER_INTERSECT)) continue;
-                inter = true;
-            }
+        if (tq >= 0 && covers_xy(Xs, Ys, 256 * qx + 128, 256 * qy + 128)) {
+            if (!(a.terms & MER_INTERSECT)) continue;
+            inter = true;
         }
         // Eq. 11 with A = left/top pixel, B = right/bottom pixel
         const size_t p = (size_t)y * it.W + px;
@@ -303,7 +325,10 @@ __device__ __forceinline__ bool edge_rows(const BItem& it, const BwdArgs& a, Bwd
             }
             if (axis == 0) ex = dLdp; else ey = dLdp;
         } else {
-            // Eq. 12: p's triangle varies (v), q's triangle is fixed (f), slice (axis, zeta)
+            // Eq. 12: p's triangle varies (v), q's triangle is fixed (f), slice (axis, zeta); q's ids were
+            // checked in pass 1
+            int vq[3];
+            tri_ids(it.tris(a), tq, it.V, vq);
             const VRec rv[3] = {load_vrec(vb + vs[0]), load_vrec(vb + vs[1]), load_vrec(vb + vs[2])};
             const VRec rq[3] = {load_vrec(vb + vq[0]), load_vrec(vb + vq[1]), load_vrec(vb + vq[2])};
             float Nv[3], Nf[3];
