@@ -47,20 +47,40 @@ MUTATIONS = {
 }
 
 
-@pytest.mark.slow
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_pins_catch_planted_mistake(name, tmp_path):
+def _run_mutation(name: str, folder: str):
+    """Builds the oracle with mutation `name` in `folder` and runs the pin suites against it; returns
+    (pytest's exit code, the tail of its output)."""
     old, new = MUTATIONS[name]
     src = open(SRC).read()
     assert src.count(old) >= 1, name  # the first occurrence: the backward (a copy may sit in the forward gradients)
-    mutated = tmp_path / "oracle_mut.c"
-    mutated.write_text(src.replace(old, new, 1))
-    lib = tmp_path / "liboracle_mut.so"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(lib),
-                    str(mutated), "-lm"], check=True)
-    env = dict(os.environ, ORACLE_LIB=str(lib))
+    mutated = os.path.join(folder, "oracle_mut.c")
+    with open(mutated, "w") as f:
+        f.write(src.replace(old, new, 1))
+    lib = os.path.join(folder, "liboracle_mut.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", lib, mutated, "-lm"],
+                   check=True)
+    env = dict(os.environ, ORACLE_LIB=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                         os.path.join(ROOT, "tests", "test_oracle_forward.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
-    assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutation_results(tmp_path_factory):
+    """Every mutation's pin run, several at once (each in its own process and folder)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    folders = {n: str(tmp_path_factory.mktemp("mut_" + n)) for n in MUTATIONS}
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as ex:
+        futures = {n: ex.submit(_run_mutation, n, folders[n]) for n in sorted(MUTATIONS)}
+        return {n: f.result() for n, f in futures.items()}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, mutation_results):
+    rc, out = mutation_results[name]
+    assert rc != 0, f"mutation {name} survived the pins:\n{out}"
