@@ -118,8 +118,8 @@ class ClockSampler:
 # one k_backward_batch launch, from an ncu capture of the same workload at 4 views (inputs already larger than
 # L2), per pixel of the launch, with the sha256 of the kernel's sources they were taken on: a launch of n views
 # moves / issues n*H*W times these.  They are reported only while the sources are unchanged.
-BACKWARD_TRAFFIC = {"bytes_per_pixel": 24.4616, "warp_instructions_per_pixel": 32.4554,
-                    "sources_sha256": "f298f8d96647fe8a60925bbef48192660acfcdc0edf5dbaaef707c5ac3189dbd",
+BACKWARD_TRAFFIC = {"bytes_per_pixel": 24.4855, "warp_instructions_per_pixel": 31.2240,
+                    "sources_sha256": "83ebab1c8fdd052ad70a3d454dfca3e006df49f0eef83942804e58dfdd4b6380",
                     "profile": "profiles/ncu_k_backward_batch_head_4x1334x2048.md"}
 
 
