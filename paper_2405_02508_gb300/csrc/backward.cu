@@ -454,7 +454,7 @@ __device__ __forceinline__ void row_pass(const BItem& it, int tx, int ty, int ro
         if (a.terms & MER_INTERIOR) {
             const float z[3] = {rv[0].zeta, rv[1].zeta, rv[2].zeta};
             const float s = B.lam[0] * z[0] + B.lam[1] * z[1] + B.lam[2] * z[2];
-            const float is = __frcp_rn(s);  // the correctly rounded 1 / s, as the division
+            const float is = rcp_nr(s);
             float b[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) b[k] = B.lam[k] * z[k] * is;

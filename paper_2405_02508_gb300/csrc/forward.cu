@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kFTW * kFTH) k_forward_grad(const mer_vertex* 
             s += B.lam[k] * z[k];
             ds += dl[k] * z[k] + B.lam[k] * tv[k][2];
         }
-        const float is = __frcp_rn(s);  // the correctly rounded 1 / s, as the division
+        const float is = rcp_nr(s);
         float b[3], db[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {

@@ -167,6 +167,17 @@ __device__ __forceinline__ float i2f_exact(int v) { return __int2float_rn(v); }
 
 __device__ __forceinline__ int floor_i(float x) { return __float2int_rd(x); }
 
+// 1 / x: the hardware's approximate reciprocal r0 (about one ulp) refined by one Newton-Raphson step,
+// r1 = r0 + r0 (1 - x r0) with both operations fused (the quadratic convergence of Newton's iteration for the
+// reciprocal; the residual is formed exactly by the FMA), so r1 is within about half an ulp of 1 / x and in
+// almost every case the correctly rounded value.  Zero, infinite and NaN inputs keep r0 (the residual of
+// 0 * inf is NaN there).  Three instructions instead of the correctly rounded reciprocal's longer sequence.
+__device__ __forceinline__ float rcp_nr(float x) {
+    const float r0 = __fdividef(1.0f, x);
+    const float r1 = __fmaf_rn(r0, __fmaf_rn(-x, r0, 1.0f), r0);
+    return isfinite(r1) ? r1 : r0;
+}
+
 // Non-negative int64 -> float, exact below 2^23 with one integer add and one float subtract (the bits of
 // 2^23 + v read as a float are exactly 2^23 + v); the general conversion otherwise.
 __device__ __forceinline__ float nonneg_ll2f_rn(long long v) {
@@ -308,7 +319,7 @@ __device__ __forceinline__ Bary screen_bary(const VRec v[3], int x, int y) {
             e[i] = __fmaf_rn(__int2float_rn(E), 1.0f / 65536.0f, lin + quad);
         }
         B.d = (e[0] + e[1]) + e[2];
-        const float inv = __frcp_rn(B.d);  // the correctly rounded 1 / d, as the division
+        const float inv = rcp_nr(B.d);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const int j = (i + 1) % 3, k = (i + 2) % 3;
@@ -332,7 +343,7 @@ __device__ __forceinline__ Bary screen_bary(const VRec v[3], int x, int y) {
         e[i] = __fmaf_rn(signed_ll2f_rn(E), 1.0f / 65536.0f, lin + quad);
     }
     B.d = (e[0] + e[1]) + e[2];
-    const float inv = __frcp_rn(B.d);  // the correctly rounded 1 / d, as the division
+    const float inv = rcp_nr(B.d);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const int j = (i + 1) % 3, k = (i + 2) % 3;

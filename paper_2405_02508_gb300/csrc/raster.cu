@@ -418,7 +418,7 @@ __device__ __forceinline__ void raster_tile(const RItem& it, int local_tile, con
             const Bary B = screen_bary(v, px, py);
             const float z0 = v[0].zeta, z1 = v[1].zeta, z2 = v[2].zeta;
             const float s = B.lam[0] * z0 + B.lam[1] * z1 + B.lam[2] * z2;
-            const float is = __frcp_rn(s);  // the correctly rounded 1 / s, as the division
+            const float is = rcp_nr(s);
             Z = is;
             b1 = B.lam[1] * z1 * is;
             b2 = B.lam[2] * z2 * is;

@@ -56,7 +56,7 @@ __device__ __forceinline__ void shade_fragment(const mer_vertex* __restrict__ vb
     const Bary B = screen_bary(v, x, y);
     float b[3];
     const float s = B.lam[0] * v[0].zeta + B.lam[1] * v[1].zeta + B.lam[2] * v[2].zeta;
-    const float is = __frcp_rn(s);  // the correctly rounded 1 / s, as the division
+    const float is = rcp_nr(s);
 #pragma unroll
     for (int k = 0; k < 3; ++k) b[k] = B.lam[k] * v[k].zeta * is;
     const int Ca = a.sh.C_attr;
