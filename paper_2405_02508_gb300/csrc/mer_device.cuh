@@ -39,7 +39,7 @@ constexpr int kBwdTileW = 32, kBwdTileH = 16;
 // vertices: with s the sign of the area and tl_i the top-left bit of edge i, X[i] x + Y[i] y + K[i] equals
 // s e_i(pixel centre of (x, y)) + tl_i - 1 modulo 2^32 for pixel indices (x, y), and inside the box that value
 // fits 31 bits, so the wrapped 32-bit evaluation is exact and the centre is covered iff all three are >= 0.
-struct TriRaster {
+struct __align__(16) TriRaster {  // 16-byte aligned: copied with 128-bit loads and stores
     int X[3], Y[3];   // snapped vertex positions; small triangle: edge i's coefficients of x and y
     float zd[3];      // zeta_i / |E_0 + E_1 + E_2|, FP32
     int flags;        // bits 0..2: edge i is top-left; bit 3: negative area; bit 4: small (32-bit path); bit 31: culled

@@ -68,13 +68,15 @@ __device__ __forceinline__ void setup_count_one(const RItem& it, int t, int tile
         it.recs[t] = r;
         return;
     }
-    mer_vertex v[3];
+    float zeta[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        v[k] = it.vpix[vid[k]];
-        if ((v[k].flags & kValid) != kValid) ok = false;
-        r.X[k] = v[k].X;
-        r.Y[k] = v[k].Y;
+    for (int k = 0; k < 3; ++k) {  // the 32-byte vertex record as two 128-bit loads (records are 32-byte aligned)
+        const float4 a = __ldg(reinterpret_cast<const float4*>(it.vpix + vid[k]));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(it.vpix + vid[k]) + 1);
+        if ((__float_as_uint(b.z) & kValid) != kValid) ok = false;  // flags
+        r.X[k] = __float_as_int(a.x);
+        r.Y[k] = __float_as_int(a.y);
+        zeta[k] = b.x;
     }
     if (!ok) { it.recs[t] = r; return; }
     const int64_t a2 = (int64_t)(r.X[1] - r.X[0]) * (r.Y[2] - r.Y[0]) - (int64_t)(r.Y[1] - r.Y[0]) * (r.X[2] - r.X[0]);
@@ -99,8 +101,8 @@ __device__ __forceinline__ void setup_count_one(const RItem& it, int t, int tile
     r.flags = fl;
     const float Df = ll2f_rn(a2 < 0 ? -a2 : a2);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) r.zd[k] = __fdiv_rn(v[k].zeta, Df);
-    r.zmax = fmaxf(v[0].zeta, fmaxf(v[1].zeta, v[2].zeta));
+    for (int k = 0; k < 3; ++k) r.zd[k] = __fdiv_rn(zeta[k], Df);
+    r.zmax = fmaxf(zeta[0], fmaxf(zeta[1], zeta[2]));
     r.bx0 = (short)x0; r.bx1 = (short)x1; r.by0 = (short)y0; r.by1 = (short)y1;
     r.K[0] = r.K[1] = r.K[2] = 0;
     if (small) {
