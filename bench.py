@@ -118,8 +118,8 @@ class ClockSampler:
 # one k_backward_batch launch, from an ncu capture of the same workload at 4 views (inputs already larger than
 # L2), per pixel of the launch, with the sha256 of the kernel's sources they were taken on: a launch of n views
 # moves / issues n*H*W times these.  They are reported only while the sources are unchanged.
-BACKWARD_TRAFFIC = {"bytes_per_pixel": 24.4855, "warp_instructions_per_pixel": 31.2240,
-                    "sources_sha256": "83ebab1c8fdd052ad70a3d454dfca3e006df49f0eef83942804e58dfdd4b6380",
+BACKWARD_TRAFFIC = {"bytes_per_pixel": 24.4699, "warp_instructions_per_pixel": 31.0864,
+                    "sources_sha256": "6c09ff0940653e50a07548f9ec794d428185f7d555c26de972205dd402d7dd76",
                     "profile": "profiles/ncu_k_backward_batch_head_4x1334x2048.md"}
 
 
